@@ -1,0 +1,314 @@
+"""Benchmark: shattered betweenness centrality on one GB300 (or N replicas).
+
+One step = one bcs_bc_shattered call (validate, connected components,
+degree-1 removal, biconnected split, identical-vertex merging, Bc-Reach over
+all pieces, map-back) on the articulation-heavy workload: 5,000 Erdos-Renyi
+blocks (sizes log-uniform 4-512, mean degree 6) glued at random cut vertices
+plus 20% of the vertices in dangling chains, seeded, FP64 dependencies.
+
+metric: effective GTEPS = n * m / T with n, m of the input graph (sources x
+undirected edges per second, the work plain Brandes would do) and T the
+device time of one step; e2e: the same through host buffers with the
+host<->device copies inside the timed region.
+
+--impl reference times the CPU oracle (plain Brandes, FP64) on the host
+cores over a bounded sample of sources of the same graph.
+
+Multi-GPU: the path needs one GPU; with --gpus N each rank runs its own
+replica of the workload (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BC GTEPS (sources·m/s), shattered vs plain Brandes on GB300, rel err ≤1e-5"
+L2_BYTES = 129 * 1024 * 1024
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=100, help="workload size in percent (100 = full)")
+    ap.add_argument("--plain-sources", type=int, default=4096)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons while the timed region runs."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except FileNotFoundError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[3 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_setup(n_gpus: int):
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if n_gpus > 1 else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if dist.get_backend() == "nccl" else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def workload(scale: int):
+    import graphgen as gg
+    g = gg.config(2, scale_pct=scale)
+    return g, {"workload": "articulation-heavy: 5000 ER blocks (log-uniform 4-512, mean deg 6) + 20% chains"
+               if scale == 100 else f"articulation-heavy at {scale}% of its blocks",
+               "n": g.n, "m": g.m, "seed": g.meta["seed"], "delta": "fp64"}
+
+
+def cpu_baseline(g, seconds: float) -> dict:
+    """The oracle (plain Brandes, FP64) on a bounded sample of sources."""
+    import oracle
+    cores = oracle.default_threads()
+    rng = np.random.default_rng(12345)
+    k = max(cores, 64)
+    t0 = time.perf_counter()
+    oracle.bc_sources(g, rng.choice(g.n, size=k, replace=False), threads=cores)
+    dt = time.perf_counter() - t0
+    k2 = int(max(k, min(g.n, k * seconds / max(dt, 1e-3))))
+    t0 = time.perf_counter()
+    oracle.bc_sources(g, rng.choice(g.n, size=k2, replace=False), threads=cores)
+    dt = time.perf_counter() - t0
+    return {"value": k2 * g.m / dt / 1e9, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+            "sample": f"{k2} seeded sources of the full graph (plain Brandes partial sums), "
+                      f"{dt:.1f} s; GTEPS = sources*m/s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_setup(args.gpus)
+    if rank != 0:
+        return
+    g, cfg = workload(args.scale)
+    import oracle
+    cores = oracle.default_threads()
+    rng = np.random.default_rng(777)
+    # size one step to about cpu_seconds / (steps + warmup) of CPU time
+    probe = max(cores, 32)
+    t0 = time.perf_counter()
+    oracle.bc_sources(g, rng.choice(g.n, size=probe, replace=False), threads=cores)
+    per_src = (time.perf_counter() - t0) / probe
+    budget = max(2.0, min(60.0, 120.0 / max(1, args.steps + args.warmup)))
+    k = int(max(cores, min(g.n, budget / max(per_src, 1e-6))))
+    for _ in range(args.warmup):
+        oracle.bc_sources(g, rng.choice(g.n, size=k, replace=False), threads=cores)
+    times = []
+    for _ in range(args.steps):
+        src = rng.choice(g.n, size=k, replace=False)
+        t0 = time.perf_counter()
+        oracle.bc_sources(g, src, threads=cores)
+        times.append(time.perf_counter() - t0)
+    T = sum(times)
+    value = k * g.m * args.steps / T / 1e9
+    line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {**cfg, "sample": f"{k} sources per step"},
+            "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                             "sample": f"{k} seeded sources per step of the full graph"},
+            "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_setup(args.gpus)
+    torch.cuda.set_device(local)
+    import paper_1209_6007_gb300 as bcs
+    bcs.load()
+    g, cfg = workload(args.scale)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bcs.bc_shattered(rp, col)
+    torch.cuda.synchronize()
+    stage_sum = {}
+    launches = 0
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    dev_ms = 0.0
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        bc = bcs.bc_shattered(rp, col)
+        ev1.record(stream)
+        ev1.synchronize()
+        dev_ms += ev0.elapsed_time(ev1)
+        st = bcs.last_stats()
+        launches += int(st["kernel_launches"])
+        for k, v in st.items():
+            if k.startswith("ms_"):
+                stage_sum[k] = stage_sum.get(k, 0.0) + v
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t_wall
+    barrier(world)
+    clk = clocks.stop()
+    T = max_over_ranks(dev_ms / 1e3, world)
+    nm = float(g.n) * float(g.m)
+    value = world * nm * args.steps / T / 1e9
+    stages = {k: v / args.steps for k, v in stage_sum.items()}
+    st = bcs.last_stats()
+
+    # end to end through host buffers
+    e2e = None
+    if not args.no_e2e:
+        for _ in range(2):
+            bcs.bc_shattered(g.row_ptr, g.col)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            bcs.bc_shattered(g.row_ptr, g.col)
+        te = max_over_ranks(time.perf_counter() - t0, world)
+        e2e = {"value": world * nm * args.steps / te / 1e9, "unit": "GTEPS",
+               "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes), "d2h_bytes_per_step": int(g.n * 8)}
+
+    # plain Brandes on a sample of sources (same kernels, no shattering)
+    plain = None
+    if args.plain_sources > 0:
+        rng = np.random.default_rng(99)
+        src = rng.choice(g.n, size=min(args.plain_sources, g.n), replace=False)
+        bcs.bc_sources(rp, col, src)
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        bcs.bc_sources(rp, col, src)
+        ev1.record(stream)
+        ev1.synchronize()
+        tp = ev0.elapsed_time(ev1) / 1e3
+        plain = {"gteps": len(src) * g.m / tp / 1e9, "sources": int(len(src)), "seconds": tp}
+
+    # fp32-delta variant of the same step
+    fp32 = None
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    bcs.bc_shattered(rp, col, delta_fp32=True)
+    ev0.record(stream)
+    b32 = bcs.bc_shattered(rp, col, delta_fp32=True)
+    ev1.record(stream)
+    ev1.synchronize()
+    t32 = ev0.elapsed_time(ev1) / 1e3
+    ref = bc.double()
+    err32 = float((b32 - ref).abs().max() / max(1.0, float(ref.abs().max())))
+    fp32 = {"gteps": nm / t32 / 1e9, "rel_err_vs_fp64": err32}
+
+    # roofline of the dominant kernel class (Bc-Reach small-component path):
+    # algorithmic bytes = each piece's CSR read once per source plus the
+    # per-vertex state written and re-read once per source
+    ms_small = stages.get("ms_bcreach_small", 0.0) + stages.get("ms_bcreach_large", 0.0)
+    se = float(st["work_sources_entries"])
+    algo_bytes = se * 4.0 * 2 + float(st["n_merged"]) * 0.0
+    roof = {"bound": "hbm", "achieved": (algo_bytes / (ms_small / 1e3) / 1e9) if ms_small > 0 else None,
+            "peak": hbm_peak, "unit": "GB/s", "traffic": None, "kernel": "bcreach (small+large)",
+            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"}
+    if roof["achieved"]:
+        roof["frac"] = roof["achieved"] / hbm_peak
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {**cfg, "l2": "flushed between timed steps (256 MB write)",
+                           "parallelism": f"{world} replica(s)"},
+                "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
+                "stages_ms": stages, "pieces": int(st["n_pieces"]), "merged_vertices": int(st["n_merged"]),
+                "work_nm_pieces": float(st["work_nm"]), "plain": plain,
+                "speedup_vs_plain": (value / plain["gteps"]) if plain else None, "fp32_delta": fp32,
+                "wall_s": wall}
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
+        print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

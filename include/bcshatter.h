@@ -1,0 +1,189 @@
+/*
+ * bcshatter.h - C ABI of the GB300 shattered betweenness-centrality library.
+ *
+ * The library computes vertex betweenness centrality (BC) of an undirected,
+ * unweighted, loop-free graph, as defined by Eq. 1 of Sariyuce, Saule, Kaya
+ * and Catalyurek, "Shattering and Compressing Networks for Centrality
+ * Analysis" (Section 2.1):
+ *
+ *     bc[v] = sum over ordered pairs (s, t), s != v != t, s != t, of
+ *             sigma_st(v) / sigma_st
+ *
+ * (ordered pairs, no normalisation; unreachable pairs add nothing; a vertex
+ * alone in its connected component gets 0).
+ *
+ * Graph input (Section 2 and Section 4: "compressed row storage using 32-bit
+ * data types"): a symmetric CSR.  row_ptr has n+1 int64 entries with
+ * row_ptr[0] = 0 and row_ptr[n] = nnz; col has nnz int32 vertex ids.  Every
+ * undirected edge {u,v} appears as both u->v and v->u, rows are sorted in
+ * strictly ascending order (no duplicate entries) and there are no
+ * self-loops.  The library checks all of this and returns BCS_EINVAL when it
+ * does not hold.  n may be 0 (nothing is computed, BCS_OK).
+ *
+ * Memory: every pointer argument is caller-owned and is never freed or kept
+ * by the library after the call returns.  When csr->on_device is 1, row_ptr,
+ * col and the bc_out array of the call are device pointers on the selected
+ * device; otherwise all of them are host pointers and the library copies
+ * through device memory it allocates itself.  Outputs are written only when
+ * the call returns BCS_OK.
+ *
+ * Streams: all device work of a call is issued on opts->stream (a
+ * cudaStream_t, NULL = the legacy default stream).  The calls are
+ * synchronous: when they return, every output has been written.
+ *
+ * Errors: every call returns BCS_OK (0) or a negative BCS_E* code;
+ * bcs_last_error() gives a message for the calling thread's last failure.
+ * Calls from several host threads are allowed; they share no mutable state
+ * apart from the per-device memory pool.
+ */
+#ifndef BCSHATTER_H
+#define BCSHATTER_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BCS_OK 0
+#define BCS_EINVAL (-1)    /* malformed CSR or argument */
+#define BCS_ENOMEM (-2)    /* device or host allocation failed */
+#define BCS_ECUDA (-3)     /* a CUDA runtime call failed */
+#define BCS_ETIMEOUT (-4)  /* a bounded device-side wait ran out */
+#define BCS_EOVERFLOW (-5) /* path counts left the range the kernels can scale */
+#define BCS_ENODEV (-6)    /* no usable CUDA device */
+
+/* Shattering / compression steps (the combination letters of Section 4.2). */
+#define BCS_STEP_D 1u /* degree-1 vertices, Section 3.3.1 */
+#define BCS_STEP_A 2u /* articulation vertices and bridges, Sections 3.2.1-3.2.2 */
+#define BCS_STEP_I 4u /* identical vertices (type I and II), Section 3.3.3 */
+#define BCS_STEPS_ALL 7u
+
+typedef struct bcs_csr {
+  int64_t n;              /* number of vertices */
+  int64_t nnz;            /* number of CSR entries (2 x undirected edges) */
+  const int64_t *row_ptr; /* n+1 row offsets */
+  const int32_t *col;     /* nnz neighbour ids */
+  int32_t on_device;      /* 1: row_ptr, col and bc_out are device pointers */
+} bcs_csr;
+
+typedef struct bcs_opts {
+  uint32_t steps;     /* BCS_STEP_* mask for bcs_bc_shattered / bcs_shatter */
+  int32_t delta_fp32; /* 1: dependency recurrence (Eq. 3) in FP32; path counts
+                         and the bc sums stay FP64 */
+  int32_t autotune;   /* 1: pick the small-component work split by timing
+                         candidates once per shape and caching the choice */
+  int32_t device;     /* CUDA device ordinal; -1 = the current device */
+  void *stream;       /* cudaStream_t for all device work; NULL = default */
+  int64_t max_wait;   /* reserved (0) */
+} bcs_opts;
+
+/* Per-call statistics of the calling thread's last successful call. */
+typedef struct bcs_stats {
+  int64_t n_pieces;        /* components handed to Bc-Reach */
+  int64_t n_slots;         /* vertex copies over all pieces before merging */
+  int64_t n_merged;        /* vertices over all pieces after identical merging */
+  int64_t n_entries;       /* CSR entries over all pieces after merging */
+  int64_t peel_rounds;     /* degree-1 removal rounds */
+  int64_t n_small_items;   /* shared-memory work items */
+  int64_t n_large_sources; /* sources run on the global-memory path */
+  int64_t kernel_launches; /* kernels this call launched */
+  double work_nm;          /* sum over pieces of n_c * m_c (m_c undirected) */
+  double work_sources_entries; /* sum over processed sources of the piece's CSR entries */
+  double ms_total;         /* wall time of the call, host clock */
+  double ms_upload;        /* host -> device copies of the input */
+  double ms_validate;      /* CSR check */
+  double ms_cc;            /* connected components */
+  double ms_peel;          /* degree-1 removal */
+  double ms_blocks;        /* biconnected split, host side, incl. copies */
+  double ms_ident;         /* identical-vertex merging */
+  double ms_plan;          /* work list */
+  double ms_bcreach_small; /* Bc-Reach, shared-memory kernel */
+  double ms_bcreach_large; /* Bc-Reach, global-memory kernel */
+  double ms_mapback;       /* bc accumulation and map back */
+  double ms_download;      /* device -> host copy of bc */
+} bcs_stats;
+
+/*
+ * Plain Brandes (Algorithm 1, Bc-Org) on the whole graph, nothing shattered:
+ * bc_out[v] for all n vertices (FP64, n entries).
+ */
+int bcs_bc_plain(const bcs_csr *csr, const bcs_opts *opts, double *bc_out);
+
+/*
+ * Shattered and compressed BC (Section 3): the steps in opts->steps are
+ * applied once in the order D, A, I; Bc-Reach (Algorithm 2, with the
+ * identical-vertex terms of Section 3.3.3) runs on every piece; the piece
+ * scores are mapped back with Eq. 5 (bc[v] = sum over copies v' of v of
+ * bc'[v']) plus the closed-form terms of the removed vertices.  The result
+ * equals Eq. 1 on the input graph (Theorem 1 and its corollaries).
+ */
+int bcs_bc_shattered(const bcs_csr *csr, const bcs_opts *opts, double *bc_out);
+
+/*
+ * Partial Brandes sum over a list of k sources (Eq. 2):
+ * bc_out[v] = sum_{i<k} delta_{src[i]}(v), with delta_s(s) taken as 0.
+ * src is a host array of k ids in [0, n) (repeats allowed).
+ */
+int bcs_bc_sources(const bcs_csr *csr, const int64_t *src, int64_t k, const bcs_opts *opts,
+                   double *bc_out);
+
+/*
+ * Single-source Brandes for tests (Algorithm 1, one source s): host arrays
+ * of n entries each: d (BFS distance, -1 unreachable), sigma as
+ * sigma_mant * 2^sigma_exp2 (sigma_mant 0 when unreachable) and delta_s(v)
+ * (Eq. 3; delta_s(s) as computed by the recursion).  Any output may be NULL.
+ */
+int bcs_debug_sssp(const bcs_csr *csr, int64_t s, const bcs_opts *opts, int32_t *d,
+                   double *sigma_mant, int32_t *sigma_exp2, double *delta);
+
+/* The pieces bcs_shatter returns (library-owned, host memory). */
+typedef struct bcs_components bcs_components;
+
+typedef struct bcs_components_view {
+  int64_t n;         /* vertices of the input graph */
+  int64_t n_pieces;  /* pieces (components of the shattered graph) */
+  int64_t n_merged;  /* vertices over all pieces after identical merging */
+  int64_t n_entries; /* local CSR entries over all pieces */
+  int64_t n_members; /* (piece, original vertex) slots before merging */
+  const int64_t *piece_vtx_off;   /* n_pieces+1: piece p owns merged vertices
+                                     [piece_vtx_off[p], piece_vtx_off[p+1]) */
+  const int64_t *piece_N;         /* n_pieces: size of the connected
+                                     component of the input the piece came from */
+  const int64_t *row_ptr;         /* n_merged+1: global offsets into col */
+  const int32_t *col;             /* n_entries: neighbour ids local to the piece */
+  const int32_t *org;             /* n_merged: original id of the kept vertex */
+  const int32_t *reach;           /* n_merged: reach (Section 3.2) */
+  const int32_t *ident;           /* n_merged: ident (Section 3.3.3) */
+  const int64_t *member_off;      /* n_merged+1 into member */
+  const int32_t *member;          /* n_members: original ids each merged vertex
+                                     stands for (itself included), ascending */
+  const int64_t *bc_pre;          /* n: exact integer terms of the vertices
+                                     removed by degree-1 compression */
+  const double *bc_corr;          /* n_merged: identical-vertex terms of
+                                     Section 3.3.3 added to every member */
+} bcs_components_view;
+
+/* Run the steps of opts->steps and return the pieces (D, A, I applied once,
+ * in that order).  *out must be freed with bcs_components_free. */
+int bcs_shatter(const bcs_csr *csr, const bcs_opts *opts, bcs_components **out);
+
+/* Fill *view with pointers into c (valid until bcs_components_free). */
+int bcs_components_get(const bcs_components *c, bcs_components_view *view);
+
+void bcs_components_free(bcs_components *c);
+
+/* Statistics of the calling thread's last successful BC call. */
+int bcs_last_stats(bcs_stats *out);
+
+/* Message for the calling thread's last error ("" if none). */
+const char *bcs_last_error(void);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int bcs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BCSHATTER_H */

@@ -1,0 +1,633 @@
+// abi.cpp - the extern "C" entry points declared in include/bcshatter.h.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <set>
+
+#include "common.h"
+
+namespace bcs {
+
+static thread_local std::string t_err;
+static thread_local bcs_stats t_stats{};
+static thread_local bool t_stats_valid = false;
+
+void set_error(const std::string &msg) { t_err = msg; }
+const std::string &get_error() { return t_err; }
+
+StageTimer::StageTimer(cudaStream_t stream) : s(stream) {
+  cudaEventCreate(&a);
+  cudaEventCreate(&b);
+}
+StageTimer::~StageTimer() {
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+}
+void StageTimer::start() { cudaEventRecord(a, s); }
+double StageTimer::stop_ms() {
+  float ms = 0.f;
+  cudaEventRecord(b, s);
+  cudaEventSynchronize(b);
+  cudaEventElapsedTime(&ms, a, b);
+  return (double)ms;
+}
+
+static std::mutex g_pool_mu;
+static std::set<int> g_pool_ready;
+
+int make_ctx(const bcs_opts *opts, Ctx *ctx) {
+  int count = 0;
+  cudaError_t e = cudaGetDeviceCount(&count);
+  if (e != cudaSuccess || count == 0) {
+    cudaGetLastError();
+    set_error(std::string("no CUDA device: ") + (e != cudaSuccess ? cudaGetErrorString(e) : "count is 0"));
+    return BCS_ENODEV;
+  }
+  int dev = 0;
+  BCS_CUDA(cudaGetDevice(&dev));
+  if (opts && opts->device >= 0) {
+    if (opts->device >= count) {
+      set_error("opts->device out of range");
+      return BCS_EINVAL;
+    }
+    dev = opts->device;
+  }
+  BCS_CUDA(cudaSetDevice(dev));
+  ctx->device = dev;
+  BCS_CUDA(cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  int optin = 0;
+  BCS_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  ctx->smem_optin = (size_t)optin;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool_ready.count(dev)) {
+      cudaMemPool_t pool;
+      BCS_CUDA(cudaDeviceGetDefaultMemPool(&pool, dev));
+      uint64_t thr = UINT64_MAX;
+      BCS_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+      g_pool_ready.insert(dev);
+    }
+  }
+  ctx->stream = opts ? (cudaStream_t)opts->stream : (cudaStream_t)0;
+  return BCS_OK;
+}
+
+// Restores the caller's current device when a call ends.
+struct DeviceGuard {
+  int prev = -1;
+  DeviceGuard() {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      prev = -1;
+      cudaGetLastError();
+    }
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+static double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ------------------------------------------------------------ input
+static int check_csr(const bcs_csr *g) {
+  if (!g) {
+    set_error("csr is NULL");
+    return BCS_EINVAL;
+  }
+  if (g->n < 0 || g->nnz < 0) {
+    set_error("negative n or nnz");
+    return BCS_EINVAL;
+  }
+  if (g->n >= (int64_t)INT32_MAX - 2) {
+    set_error("n does not fit 32-bit vertex ids");
+    return BCS_EINVAL;
+  }
+  if (g->n > 0 && (!g->row_ptr || (g->nnz > 0 && !g->col))) {
+    set_error("row_ptr or col is NULL");
+    return BCS_EINVAL;
+  }
+  if (g->n > 0 && !g->on_device) {
+    if (g->row_ptr[0] != 0 || g->row_ptr[g->n] != g->nnz) {
+      set_error("row_ptr[0] must be 0 and row_ptr[n] must equal nnz");
+      return BCS_EINVAL;
+    }
+  }
+  return BCS_OK;
+}
+
+struct Input {
+  DevGraph g;
+  DBuf<int64_t> rp;
+  DBuf<int32_t> col;
+};
+
+static int upload_and_validate(Ctx &ctx, const bcs_csr *h, Input *in) {
+  in->g.n = h->n;
+  in->g.nnz = h->nnz;
+  if (h->on_device) {
+    in->g.rp = h->row_ptr;
+    in->g.col = h->col;
+  } else {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    BCS_TRY(in->rp.alloc(h->n + 1, ctx.stream));
+    BCS_TRY(in->col.alloc(h->nnz, ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(in->rp.p, h->row_ptr, (h->n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, ctx.stream));
+    if (h->nnz)
+      BCS_CUDA(cudaMemcpyAsync(in->col.p, h->col, h->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, ctx.stream));
+    in->g.rp = in->rp.p;
+    in->g.col = in->col.p;
+    ctx.stats.ms_upload = tm.stop_ms();
+  }
+  StageTimer tm(ctx.stream);
+  tm.start();
+  DBuf<int> flags;
+  BCS_TRY(flags.alloc(1, ctx.stream));
+  BCS_TRY(launch_validate(ctx, in->g, flags.p));
+  int f = 0;
+  BCS_CUDA(cudaMemcpyAsync(&f, flags.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  ctx.stats.ms_validate = tm.stop_ms();
+  if (f) {
+    std::string m = "malformed CSR:";
+    if (f & 1) m += " offsets or ids out of range;";
+    if (f & 2) m += " self-loop;";
+    if (f & 4) m += " row not strictly ascending (unsorted or duplicate entry);";
+    if (f & 8) m += " not symmetric;";
+    set_error(m);
+    return BCS_EINVAL;
+  }
+  return BCS_OK;
+}
+
+static int output_bc(Ctx &ctx, const bcs_csr *h, const double *d_bc, double *bc_out) {
+  if (h->on_device) {
+    if (d_bc != bc_out)
+      BCS_CUDA(cudaMemcpyAsync(bc_out, d_bc, h->n * sizeof(double), cudaMemcpyDeviceToDevice, ctx.stream));
+    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  } else {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    BCS_CUDA(cudaMemcpyAsync(bc_out, d_bc, h->n * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
+    ctx.stats.ms_download = tm.stop_ms();
+  }
+  return BCS_OK;
+}
+
+// max degree of the input (bound on path-count growth per BFS level)
+static int max_degree(Ctx &ctx, const bcs_csr *h, const DevGraph &g, int64_t *out) {
+  int64_t mx = 0;
+  if (!h->on_device) {
+    for (int64_t v = 0; v < h->n; v++) mx = std::max(mx, h->row_ptr[v + 1] - h->row_ptr[v]);
+  } else {
+    std::vector<int64_t> rp(h->n + 1);
+    BCS_CUDA(cudaMemcpyAsync(rp.data(), g.rp, (h->n + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+    for (int64_t v = 0; v < h->n; v++) mx = std::max(mx, rp[v + 1] - rp[v]);
+  }
+  *out = mx;
+  return BCS_OK;
+}
+
+// ------------------------------------------------------------ plain
+static int plain_impl(Ctx &ctx, const bcs_csr *h, const int64_t *src, int64_t k, double *bc_out, BcPlanOpts po) {
+  Input in;
+  BCS_TRY(upload_and_validate(ctx, h, &in));
+  DBuf<double> bc;
+  double *d_bc = bc_out;
+  if (!h->on_device) {
+    BCS_TRY(bc.alloc(h->n, ctx.stream));
+    d_bc = bc.p;
+  }
+  BCS_CUDA(cudaMemsetAsync(d_bc, 0, h->n * sizeof(double), ctx.stream));
+  int64_t mxd = 0;
+  BCS_TRY(max_degree(ctx, h, in.g, &mxd));
+  std::vector<CompDesc> comps(1);
+  comps[0] = CompDesc{0, 0, (int32_t)h->n, (int32_t)mxd, h->nnz, (double)std::max<int64_t>(mxd, 1)};
+  BcInput bi;
+  bi.row = in.g.rp;
+  bi.col = in.g.col;
+  bi.bcp = d_bc;
+  po.sources = src;
+  po.nsources = k;
+  BCS_TRY(run_bcreach(ctx, comps, bi, po));
+  ctx.stats.n_pieces = 1;
+  ctx.stats.n_slots = ctx.stats.n_merged = h->n;
+  ctx.stats.n_entries = h->nnz;
+  ctx.stats.work_nm = (double)h->n * (double)(h->nnz / 2);
+  return output_bc(ctx, h, d_bc, bc_out);
+}
+
+// ------------------------------------------------------------ shattered
+struct Shattered {
+  DBuf<int64_t> bcpre;
+  HostPieces hp;
+  DevMerged merged;
+  std::vector<CompDesc> comps;
+};
+
+static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t steps, Shattered *S) {
+  const int64_t n = h->n;
+  const bool D = steps & BCS_STEP_D, A = steps & BCS_STEP_A, I = steps & BCS_STEP_I;
+  DBuf<int32_t> label, reach;
+  DBuf<int64_t> N;
+  DBuf<uint8_t> alive;
+  BCS_TRY(label.alloc(n, ctx.stream));
+  BCS_TRY(N.alloc(n, ctx.stream));
+  BCS_TRY(reach.alloc(n, ctx.stream));
+  BCS_TRY(alive.alloc(n, ctx.stream));
+  BCS_TRY(S->bcpre.alloc(n, ctx.stream));
+  {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    BCS_TRY(launch_cc(ctx, in.g, label.p, N.p));
+    ctx.stats.ms_cc = tm.stop_ms();
+  }
+  {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    if (D) {
+      BCS_TRY(run_peel(ctx, in.g, N.p, alive.p, reach.p, S->bcpre.p));
+    } else {
+      BCS_CUDA(cudaMemsetAsync(alive.p, 1, n, ctx.stream));
+      BCS_TRY(launch_fill_i32(ctx, reach.p, n, 1));
+      BCS_CUDA(cudaMemsetAsync(S->bcpre.p, 0, n * sizeof(int64_t), ctx.stream));
+    }
+    ctx.stats.ms_peel = tm.stop_ms();
+  }
+  {
+    // pieces on the host
+    StageTimer tm(ctx.stream);
+    tm.start();
+    std::vector<uint8_t> h_alive(n);
+    std::vector<int32_t> h_reach(n), h_label(n);
+    std::vector<int64_t> h_N(n);
+    std::vector<int64_t> h_rp;
+    std::vector<int32_t> h_col;
+    BCS_CUDA(cudaMemcpyAsync(h_alive.data(), alive.p, n, cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(h_reach.data(), reach.p, n * 4, cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(h_label.data(), label.p, n * 4, cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(h_N.data(), N.p, n * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    const int64_t *rp = h->row_ptr;
+    const int32_t *col = h->col;
+    if (h->on_device) {
+      h_rp.resize(n + 1);
+      h_col.resize(h->nnz);
+      BCS_CUDA(cudaMemcpyAsync(h_rp.data(), h->row_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, ctx.stream));
+      if (h->nnz) BCS_CUDA(cudaMemcpyAsync(h_col.data(), h->col, h->nnz * 4, cudaMemcpyDeviceToHost, ctx.stream));
+      rp = h_rp.data();
+      col = h_col.data();
+    }
+    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+    BCS_TRY(host_build_pieces(n, rp, col, h_alive.data(), h_reach.data(), h_N.data(), h_label.data(), A, &S->hp));
+    ctx.stats.ms_blocks = tm.stop_ms();
+  }
+  {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    BCS_TRY(device_merge(ctx, S->hp, I, &S->merged));
+    ctx.stats.ms_ident = tm.stop_ms();
+  }
+  // component descriptors
+  const HostPieces &hp = S->hp;
+  const DevMerged &m = S->merged;
+  const int64_t P = hp.npieces();
+  S->comps.resize(P);
+  double work_nm = 0.0;
+  for (int64_t p = 0; p < P; p++) {
+    int64_t mx = 1;
+    for (int64_t x = hp.piece_off[p]; x < hp.piece_off[p + 1]; x++) mx = std::max(mx, hp.srow[x + 1] - hp.srow[x]);
+    CompDesc c;
+    c.vtx_off = m.h_piece_off[p];
+    c.row_off = m.h_piece_off[p];
+    c.n = (int32_t)(m.h_piece_off[p + 1] - m.h_piece_off[p]);
+    c.maxdeg = (int32_t)mx;
+    c.nnz = m.h_piece_ent[p];
+    c.fan = (double)mx;
+    S->comps[p] = c;
+    work_nm += (double)c.n * (double)(c.nnz / 2);
+  }
+  ctx.stats.n_pieces = P;
+  ctx.stats.n_slots = hp.nslots();
+  ctx.stats.n_merged = m.nmerged;
+  ctx.stats.n_entries = m.nentries;
+  ctx.stats.work_nm = work_nm;
+  return BCS_OK;
+}
+
+static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double *bc_out) {
+  Input in;
+  BCS_TRY(upload_and_validate(ctx, h, &in));
+  const uint32_t steps = o ? o->steps : BCS_STEPS_ALL;
+  Shattered S;
+  BCS_TRY(shatter_impl(ctx, h, in, steps, &S));
+  DevMerged &m = S.merged;
+  BcInput bi;
+  bi.row = m.mrow.p;
+  bi.col = m.mcol.p;
+  bi.reach = (steps & (BCS_STEP_D | BCS_STEP_A)) ? m.mreach.p : nullptr;
+  bi.ident = (steps & BCS_STEP_I) ? m.mident.p : nullptr;
+  bi.bcp = m.mcorr.p;  // starts with the identical-vertex terms
+  BcPlanOpts po;
+  po.fp32_delta = o && o->delta_fp32;
+  BCS_TRY(run_bcreach(ctx, S.comps, bi, po));
+  DBuf<double> bc;
+  double *d_bc = bc_out;
+  if (!h->on_device) {
+    BCS_TRY(bc.alloc(h->n, ctx.stream));
+    d_bc = bc.p;
+  }
+  {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    BCS_TRY(launch_bc_init(ctx, h->n, S.bcpre.p, d_bc));
+    BCS_TRY(launch_mapback(ctx, m.nslots, m.slot_org.p, m.slot_to_m.p, m.mcorr.p, d_bc));
+    ctx.stats.ms_mapback = tm.stop_ms();
+  }
+  return output_bc(ctx, h, d_bc, bc_out);
+}
+
+}  // namespace bcs
+
+// ================================================================ C ABI
+using namespace bcs;
+
+struct bcs_components {
+  int64_t n = 0;
+  std::vector<int64_t> piece_vtx_off, piece_N, row_ptr, member_off, bc_pre;
+  std::vector<int32_t> col, org, reach, ident, member;
+  std::vector<double> bc_corr;
+};
+
+template <class F>
+static int guarded(const bcs_opts *opts, F &&body) {
+  DeviceGuard dg;
+  try {
+    double t0 = now_ms();
+    Ctx ctx;
+    int rc = make_ctx(opts, &ctx);
+    if (rc != BCS_OK) return rc;
+    rc = body(ctx);
+    if (rc == BCS_OK) {
+      ctx.stats.ms_total = now_ms() - t0;
+      ctx.stats.kernel_launches = ctx.launches;
+      t_stats = ctx.stats;
+      t_stats_valid = true;
+    }
+    return rc;
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed");
+    return BCS_ENOMEM;
+  } catch (const std::exception &e) {
+    set_error(std::string("internal error: ") + e.what());
+    return BCS_ECUDA;
+  }
+}
+
+extern "C" {
+
+__attribute__((visibility("default"))) int bcs_bc_plain(const bcs_csr *csr, const bcs_opts *opts, double *bc_out) {
+  int rc = check_csr(csr);
+  if (rc != BCS_OK) return rc;
+  if (csr->n == 0) return BCS_OK;
+  if (!bc_out) {
+    set_error("bc_out is NULL");
+    return BCS_EINVAL;
+  }
+  return guarded(opts, [&](Ctx &ctx) {
+    BcPlanOpts po;
+    po.fp32_delta = opts && opts->delta_fp32;
+    return plain_impl(ctx, csr, nullptr, 0, bc_out, po);
+  });
+}
+
+__attribute__((visibility("default"))) int bcs_bc_shattered(const bcs_csr *csr, const bcs_opts *opts,
+                                                            double *bc_out) {
+  int rc = check_csr(csr);
+  if (rc != BCS_OK) return rc;
+  if (csr->n == 0) return BCS_OK;
+  if (!bc_out) {
+    set_error("bc_out is NULL");
+    return BCS_EINVAL;
+  }
+  if (opts && (opts->steps & ~BCS_STEPS_ALL)) {
+    set_error("unknown bits in opts->steps");
+    return BCS_EINVAL;
+  }
+  return guarded(opts, [&](Ctx &ctx) { return shattered_impl(ctx, csr, opts, bc_out); });
+}
+
+__attribute__((visibility("default"))) int bcs_bc_sources(const bcs_csr *csr, const int64_t *src, int64_t k,
+                                                          const bcs_opts *opts, double *bc_out) {
+  int rc = check_csr(csr);
+  if (rc != BCS_OK) return rc;
+  if (k < 0 || (k > 0 && !src)) {
+    set_error("bad source list");
+    return BCS_EINVAL;
+  }
+  for (int64_t i = 0; i < k; i++)
+    if (src[i] < 0 || src[i] >= csr->n) {
+      set_error("source id out of range");
+      return BCS_EINVAL;
+    }
+  if (csr->n == 0) return BCS_OK;
+  if (!bc_out) {
+    set_error("bc_out is NULL");
+    return BCS_EINVAL;
+  }
+  return guarded(opts, [&](Ctx &ctx) {
+    BcPlanOpts po;
+    po.fp32_delta = opts && opts->delta_fp32;
+    if (k == 0) {
+      Input in;
+      BCS_TRY(upload_and_validate(ctx, csr, &in));
+      if (csr->on_device) {
+        BCS_CUDA(cudaMemsetAsync(bc_out, 0, csr->n * sizeof(double), ctx.stream));
+        BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+      } else {
+        std::memset(bc_out, 0, csr->n * sizeof(double));
+      }
+      return BCS_OK;
+    }
+    return plain_impl(ctx, csr, src, k, bc_out, po);
+  });
+}
+
+__attribute__((visibility("default"))) int bcs_debug_sssp(const bcs_csr *csr, int64_t s, const bcs_opts *opts,
+                                                          int32_t *d, double *sigma_mant, int32_t *sigma_exp2,
+                                                          double *delta) {
+  int rc = check_csr(csr);
+  if (rc != BCS_OK) return rc;
+  if (s < 0 || s >= csr->n) {
+    set_error("source out of range");
+    return BCS_EINVAL;
+  }
+  return guarded(opts, [&](Ctx &ctx) {
+    const int64_t n = csr->n;
+    DBuf<int32_t> dd, de;
+    DBuf<double> ds, ddl, bc;
+    BCS_TRY(dd.alloc(n, ctx.stream));
+    BCS_TRY(de.alloc(n, ctx.stream));
+    BCS_TRY(ds.alloc(n, ctx.stream));
+    BCS_TRY(ddl.alloc(n, ctx.stream));
+    BCS_TRY(bc.alloc(n, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(dd.p, 0xFF, n * 4, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(de.p, 0, n * 4, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(ds.p, 0, n * 8, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(ddl.p, 0, n * 8, ctx.stream));
+    BcPlanOpts po;
+    po.fp32_delta = opts && opts->delta_fp32;
+    po.dbg_d = dd.p;
+    po.dbg_sig = ds.p;
+    po.dbg_exp = de.p;
+    po.dbg_delta = ddl.p;
+    bcs_csr hcsr = *csr;
+    // outputs of this call are host arrays; the bc sum goes to a scratch array
+    const bool dev_in = csr->on_device != 0;
+    int64_t src = s;
+    Input in;
+    BCS_TRY(upload_and_validate(ctx, csr, &in));
+    int64_t mxd = 0;
+    BCS_TRY(max_degree(ctx, csr, in.g, &mxd));
+    std::vector<CompDesc> comps(1);
+    comps[0] = CompDesc{0, 0, (int32_t)n, (int32_t)mxd, csr->nnz, (double)std::max<int64_t>(mxd, 1)};
+    BcInput bi;
+    bi.row = in.g.rp;
+    bi.col = in.g.col;
+    bi.bcp = bc.p;
+    BCS_CUDA(cudaMemsetAsync(bc.p, 0, n * 8, ctx.stream));
+    po.sources = &src;
+    po.nsources = 1;
+    (void)hcsr;
+    (void)dev_in;
+    BCS_TRY(run_bcreach(ctx, comps, bi, po));
+    if (d) BCS_CUDA(cudaMemcpyAsync(d, dd.p, n * 4, cudaMemcpyDeviceToHost, ctx.stream));
+    if (sigma_mant) BCS_CUDA(cudaMemcpyAsync(sigma_mant, ds.p, n * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    if (sigma_exp2) BCS_CUDA(cudaMemcpyAsync(sigma_exp2, de.p, n * 4, cudaMemcpyDeviceToHost, ctx.stream));
+    if (delta) BCS_CUDA(cudaMemcpyAsync(delta, ddl.p, n * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+    return BCS_OK;
+  });
+}
+
+__attribute__((visibility("default"))) int bcs_shatter(const bcs_csr *csr, const bcs_opts *opts,
+                                                       bcs_components **out) {
+  int rc = check_csr(csr);
+  if (rc != BCS_OK) return rc;
+  if (!out) {
+    set_error("out is NULL");
+    return BCS_EINVAL;
+  }
+  if (opts && (opts->steps & ~BCS_STEPS_ALL)) {
+    set_error("unknown bits in opts->steps");
+    return BCS_EINVAL;
+  }
+  *out = nullptr;
+  auto *c = new (std::nothrow) bcs_components();
+  if (!c) {
+    set_error("host allocation failed");
+    return BCS_ENOMEM;
+  }
+  c->n = csr->n;
+  if (csr->n == 0) {
+    c->piece_vtx_off.assign(1, 0);
+    c->row_ptr.assign(1, 0);
+    c->member_off.assign(1, 0);
+    *out = c;
+    return BCS_OK;
+  }
+  rc = guarded(opts, [&](Ctx &ctx) {
+    Input in;
+    BCS_TRY(upload_and_validate(ctx, csr, &in));
+    Shattered S;
+    BCS_TRY(shatter_impl(ctx, csr, in, opts ? opts->steps : BCS_STEPS_ALL, &S));
+    const DevMerged &m = S.merged;
+    const int64_t M = m.nmerged, E = m.nentries, SL = m.nslots, n = csr->n;
+    c->piece_vtx_off = m.h_piece_off;
+    c->piece_N = S.hp.piece_N;
+    c->row_ptr.resize(M + 1);
+    c->col.resize(E);
+    c->org.resize(M);
+    c->reach.resize(M);
+    c->ident.resize(M);
+    c->bc_corr.resize(M);
+    c->bc_pre.resize(n);
+    std::vector<int32_t> s2m(SL);
+    BCS_CUDA(cudaMemcpyAsync(c->row_ptr.data(), m.mrow.p, (M + 1) * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    if (E) BCS_CUDA(cudaMemcpyAsync(c->col.data(), m.mcol.p, E * 4, cudaMemcpyDeviceToHost, ctx.stream));
+    if (M) {
+      BCS_CUDA(cudaMemcpyAsync(c->org.data(), m.morg.p, M * 4, cudaMemcpyDeviceToHost, ctx.stream));
+      BCS_CUDA(cudaMemcpyAsync(c->reach.data(), m.mreach.p, M * 4, cudaMemcpyDeviceToHost, ctx.stream));
+      BCS_CUDA(cudaMemcpyAsync(c->ident.data(), m.mident.p, M * 4, cudaMemcpyDeviceToHost, ctx.stream));
+      BCS_CUDA(cudaMemcpyAsync(c->bc_corr.data(), m.mcorr.p, M * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    }
+    if (SL) BCS_CUDA(cudaMemcpyAsync(s2m.data(), m.slot_to_m.p, SL * 4, cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(c->bc_pre.data(), S.bcpre.p, n * 8, cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+    // members: pre-merge slots grouped by merged vertex (slots are ascending
+    // by original id inside a piece, so each member list comes out sorted)
+    c->member_off.assign(M + 1, 0);
+    for (int64_t x = 0; x < SL; x++) c->member_off[s2m[x] + 1]++;
+    for (int64_t i = 0; i < M; i++) c->member_off[i + 1] += c->member_off[i];
+    c->member.resize(SL);
+    std::vector<int64_t> pos(c->member_off.begin(), c->member_off.end() - 1);
+    for (int64_t x = 0; x < SL; x++) c->member[pos[s2m[x]]++] = S.hp.slot_org[x];
+    return BCS_OK;
+  });
+  if (rc != BCS_OK) {
+    delete c;
+    return rc;
+  }
+  *out = c;
+  return BCS_OK;
+}
+
+__attribute__((visibility("default"))) int bcs_components_get(const bcs_components *c, bcs_components_view *v) {
+  if (!c || !v) {
+    set_error("NULL argument");
+    return BCS_EINVAL;
+  }
+  v->n = c->n;
+  v->n_pieces = (int64_t)c->piece_vtx_off.size() - 1;
+  v->n_merged = (int64_t)c->org.size();
+  v->n_entries = (int64_t)c->col.size();
+  v->n_members = (int64_t)c->member.size();
+  v->piece_vtx_off = c->piece_vtx_off.data();
+  v->piece_N = c->piece_N.data();
+  v->row_ptr = c->row_ptr.data();
+  v->col = c->col.data();
+  v->org = c->org.data();
+  v->reach = c->reach.data();
+  v->ident = c->ident.data();
+  v->member_off = c->member_off.data();
+  v->member = c->member.data();
+  v->bc_pre = c->bc_pre.data();
+  v->bc_corr = c->bc_corr.data();
+  return BCS_OK;
+}
+
+__attribute__((visibility("default"))) void bcs_components_free(bcs_components *c) { delete c; }
+
+__attribute__((visibility("default"))) int bcs_last_stats(bcs_stats *out) {
+  if (!out) {
+    set_error("NULL argument");
+    return BCS_EINVAL;
+  }
+  if (!t_stats_valid) {
+    set_error("no successful call yet on this thread");
+    return BCS_EINVAL;
+  }
+  *out = t_stats;
+  return BCS_OK;
+}
+
+__attribute__((visibility("default"))) const char *bcs_last_error(void) { return t_err.c_str(); }
+
+__attribute__((visibility("default"))) int bcs_version(void) { return 100; }
+
+}  // extern "C"

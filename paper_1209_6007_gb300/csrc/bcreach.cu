@@ -1,0 +1,609 @@
+// bcreach.cu - Bc-Reach (Algorithm 2 with the identical-vertex terms of
+// Section 3.3.3) over many components in persistent launches.
+//
+// Per source s of a component (local ids, reach r[], ident k[]):
+//   phase 1 (BFS, Algorithm 1):  d[s] = 0, sigma[s] = 1,
+//     sigma[w] += sigma[v] * (v == s ? 1 : k[v])  for every DAG edge v -> w
+//   phase 2 (Eq. 3 with reach and ident):
+//     delta[v] = r[v] - 1 + sum_{w: d[w] = d[v]+1} sigma[v]/sigma[w] * k[w] * (1 + delta[w])
+//     bc'[v]  += r[s] * k[s] * delta[v]   for v != s
+// Phase 2 is evaluated in the equivalent "coefficient" form
+//     c[w] = k[w] (1 + delta[w]) / sigma[w],   delta[v] = r[v] - 1 + sigma[v] * sum_w c[w]
+// so that each shortest-path-DAG edge costs one addition and each vertex one
+// division.
+//
+// A group of threads (one warp up to a whole CTA) runs one source at a time,
+// level-synchronously: the BFS queue doubles as the stack of Algorithm 1 and
+// its level boundaries are kept, so phase 2 walks the levels deepest first
+// and pulls from the successors (no atomics in phase 2).
+//
+// Path counts.  sigma is FP64.  Each level carries a power-of-two exponent:
+// when a level's largest count passes 2^960 the whole level is scaled by an
+// exact power of two, and phase 2 multiplies by 2^(e[L] - e[L+1]).  Counts
+// below 2^53 are never scaled and stay exact integers.
+//
+// FP32 mode keeps delta and the per-edge sums in FP32: c is stored as an FP32
+// value relative to the binary exponent of sigma[w] (held next to it), so
+// sigma's full range is kept without FP64 arithmetic in phase 2.
+#include <algorithm>
+#include <cfloat>
+#include <numeric>
+
+#include "common.h"
+
+namespace bcs {
+
+constexpr int SMALL_THREADS = 256;
+constexpr int SMALL_MAX_GROUPS = 8;
+constexpr int LARGE_THREADS = 512;
+
+struct SmallItem {
+  int32_t comp;
+  int32_t s_begin;  // index range into the source list (or local ids)
+  int32_t s_end;
+  int32_t ngroups;  // groups per CTA (1, 2, 4, 8)
+};
+
+struct Coef32 {
+  float c;
+  int32_t e;
+};
+
+// error flags written by the kernels
+constexpr int ERR_OVERFLOW = 1;
+
+// ------------------------------------------------------------------ group
+struct Group {
+  int rank, size, bar;
+  __device__ __forceinline__ void sync() const {
+    if (size == 32) __syncwarp();
+    else asm volatile("bar.sync %0, %1;" ::"r"(bar), "r"(size) : "memory");
+  }
+};
+
+__device__ __forceinline__ double group_max(const Group &g, double x, volatile double *red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = fmax(x, __shfl_xor_sync(0xffffffffu, x, o));
+  if (g.size == 32) return x;
+  if ((g.rank & 31) == 0) red[g.rank >> 5] = x;
+  g.sync();
+  double r = red[0];
+  for (int i = 1; i < (g.size >> 5); i++) r = fmax(r, red[i]);
+  g.sync();
+  return r;
+}
+
+__device__ __forceinline__ int vld(const int32_t *p) { return *(volatile const int32_t *)p; }
+
+// binary exponent and [1,2) mantissa of a positive normal double
+__device__ __forceinline__ void split_pow2(double x, int &e, float &m) {
+  e = ilogb(x);
+  m = (float)scalbn(x, -e);
+}
+
+template <bool FP32>
+struct CoefT;
+template <>
+struct CoefT<false> {
+  using type = double;
+};
+template <>
+struct CoefT<true> {
+  using type = Coef32;
+};
+
+// State of one source, in shared (small path) or global (large path) memory.
+template <bool FP32>
+struct SrcState {
+  int32_t *d;
+  double *sig;
+  typename CoefT<FP32>::type *coef;
+  int32_t *queue;
+  int32_t *lvl_start;  // levels + 2
+  int32_t *lvl_exp;    // levels + 1
+  int *qtail;          // shared counter
+  double *red;         // shared, 16 doubles
+};
+
+struct Weights {
+  const int32_t *reach;  // local, nullable
+  const int32_t *ident;  // local, nullable
+};
+
+struct Debug {
+  int32_t *d;
+  double *sig;
+  int32_t *exp;
+  double *delta;
+};
+
+// One source of Bc-Reach over a component held as (row, col) with local ids.
+// RESET_BY_QUEUE: the state arrays start as d = -1, sigma = 0 and are put
+// back that way through the queue at the end (global-memory path); else they
+// are initialised here (shared-memory path).
+template <bool REACH, bool IDENT, bool FP32, bool ATOMIC_ACC, bool RESET_BY_QUEUE, typename RowT, typename ColT>
+__device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n, const RowT *__restrict__ row,
+                               const ColT *__restrict__ col, const Weights wt, const SrcState<FP32> st,
+                               double *acc, const double fan, int *err, const Debug *dbg) {
+  int32_t *const d = st.d;
+  double *const sig = st.sig;
+  if (!RESET_BY_QUEUE) {
+    for (int v = g.rank; v < n; v += g.size) {
+      d[v] = -1;
+      sig[v] = 0.0;
+    }
+    g.sync();
+  }
+  if (g.rank == 0) {
+    d[s] = 0;
+    sig[s] = 1.0;
+    st.queue[0] = s;
+    *st.qtail = 1;
+    st.lvl_start[0] = 0;
+    st.lvl_start[1] = 1;
+    st.lvl_exp[0] = 0;
+  }
+  g.sync();
+  // ---------------------------------------------------------- phase 1
+  int lo = 0, hi = 1, L = 0, ecur = 0;
+  double bound = 1.0;
+  for (;;) {
+    for (int i = lo + g.rank; i < hi; i += g.size) {
+      const int32_t v = st.queue[i];
+      double sv = sig[v];
+      if (IDENT && v != s) sv *= (double)wt.ident[v];
+      const RowT eb = row[v], ee = row[v + 1];
+      for (RowT e = eb; e < ee; e++) {
+        const int32_t w = (int32_t)col[e];
+        int dw = vld(d + w);
+        if (dw < 0) {
+          const int old = atomicCAS(d + w, -1, L + 1);
+          if (old < 0) {
+            const int pos = atomicAdd(st.qtail, 1);
+            st.queue[pos] = w;
+            dw = L + 1;
+          } else {
+            dw = old;
+          }
+        }
+        if (dw == L + 1) atomicAdd(sig + w, sv);
+      }
+    }
+    g.sync();
+    const int nhi = vld(st.qtail);
+    g.sync();
+    if (nhi == hi) break;
+    bound *= fan;
+    if (bound > 0x1p900) {
+      double m = 0.0;
+      for (int i = hi + g.rank; i < nhi; i += g.size) m = fmax(m, sig[st.queue[i]]);
+      m = group_max(g, m, st.red);
+      if (!(m <= DBL_MAX)) {
+        if (g.rank == 0) atomicOr(err, ERR_OVERFLOW);
+      } else if (m > 0x1p960) {
+        const int k = ilogb(m) - 959;
+        for (int i = hi + g.rank; i < nhi; i += g.size) {
+          const int32_t w = st.queue[i];
+          sig[w] = scalbn(sig[w], -k);
+        }
+        m = scalbn(m, -k);
+        ecur += k;
+      }
+      bound = m;
+      g.sync();
+    }
+    lo = hi;
+    hi = nhi;
+    L++;
+    if (g.rank == 0) {
+      st.lvl_start[L + 1] = hi;
+      st.lvl_exp[L] = ecur;
+    }
+  }
+  const int Lmax = L;
+  g.sync();
+  // ---------------------------------------------------------- phase 2
+  const double Ws = (REACH ? (double)wt.reach[s] : 1.0) * (IDENT ? (double)wt.ident[s] : 1.0);
+  for (int l = Lmax; l >= 0; l--) {
+    const int a = st.lvl_start[l], b = st.lvl_start[l + 1];
+    const int de = (l < Lmax) ? st.lvl_exp[l] - st.lvl_exp[l + 1] : 0;
+    const double scl = de == 0 ? 1.0 : (de < -1070 ? 0.0 : scalbn(1.0, de));
+    for (int i = a + g.rank; i < b; i += g.size) {
+      const int32_t v = st.queue[i];
+      const double sv = sig[v];
+      const double init = REACH ? (double)(wt.reach[v] - 1) : 0.0;
+      const double kv = IDENT ? (double)wt.ident[v] : 1.0;
+      double dv;
+      if (!FP32) {
+        double sum = 0.0;
+        if (l < Lmax) {
+          const RowT eb = row[v], ee = row[v + 1];
+          for (RowT e = eb; e < ee; e++) {
+            const int32_t w = (int32_t)col[e];
+            if (d[w] == l + 1) sum += ((const double *)st.coef)[w];
+          }
+        }
+        dv = init + sv * sum * scl;
+        ((double *)st.coef)[v] = kv * (1.0 + dv) / sv;
+      } else {
+        int ev;
+        float mv;
+        split_pow2(sv, ev, mv);
+        ev += st.lvl_exp[l];
+        float sum = 0.0f;
+        if (l < Lmax) {
+          const RowT eb = row[v], ee = row[v + 1];
+          for (RowT e = eb; e < ee; e++) {
+            const int32_t w = (int32_t)col[e];
+            if (d[w] == l + 1) {
+              const Coef32 cw = ((const Coef32 *)st.coef)[w];
+              const int x = ev - cw.e;  // <= 0: sigma[v] <= sigma[w]
+              if (x >= -126) sum = fmaf(cw.c, __int_as_float((127 + x) << 23), sum);
+            }
+          }
+        }
+        const float df = (float)init + mv * sum;
+        dv = (double)df;
+        Coef32 cv;
+        cv.c = (float)kv * (1.0f + df) / mv;
+        cv.e = ev;
+        ((Coef32 *)st.coef)[v] = cv;
+      }
+      if (v != s && dv != 0.0) {
+        if (ATOMIC_ACC) atomicAdd(acc + v, Ws * dv);
+        else acc[v] += Ws * dv;
+      }
+      if (dbg) dbg->delta[v] = dv;
+    }
+    g.sync();
+  }
+  if (dbg) {
+    for (int i = g.rank; i < hi; i += g.size) {
+      const int32_t v = st.queue[i];
+      dbg->d[v] = d[v];
+      dbg->sig[v] = sig[v];
+      dbg->exp[v] = st.lvl_exp[d[v]];
+    }
+    g.sync();
+  }
+  if (RESET_BY_QUEUE) {
+    for (int i = g.rank; i < hi; i += g.size) {
+      const int32_t v = st.queue[i];
+      d[v] = -1;
+      sig[v] = 0.0;
+    }
+    g.sync();
+  }
+}
+
+// ---------------------------------------------------------- small path
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// bytes of shared memory a component needs with `ng` concurrent sources
+__host__ __device__ inline size_t small_smem_bytes(int64_t n, int64_t nnz, int ng, bool reach, bool ident) {
+  size_t b = align16((size_t)(n + 1) * 4) + align16((size_t)nnz * 4);
+  if (reach) b += align16((size_t)n * 4);
+  if (ident) b += align16((size_t)n * 4);
+  b += align16((size_t)n * 8);  // accumulator
+  size_t per = align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 2;
+  return b + per * (size_t)ng;
+}
+
+template <bool REACH, bool IDENT, bool FP32>
+__global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
+    const SmallItem *__restrict__ items, int nitems, int *item_counter, const CompDesc *__restrict__ comps,
+    const int64_t *__restrict__ g_row, const int32_t *__restrict__ g_col, const int32_t *__restrict__ g_reach,
+    const int32_t *__restrict__ g_ident, const int64_t *__restrict__ srcs, double *bcp, int32_t *lvl_scratch,
+    int lvl_stride, int *err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  __shared__ int s_qtail[SMALL_MAX_GROUPS];
+  __shared__ double s_red[SMALL_MAX_GROUPS][16];
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(item_counter, 1);
+    __syncthreads();
+    const int it = s_item;
+    __syncthreads();
+    if (it >= nitems) break;
+    const SmallItem item = items[it];
+    const CompDesc c = comps[item.comp];
+    const int n = c.n;
+    const int nnz = (int)c.nnz;
+    unsigned char *p = smem;
+    int32_t *row = (int32_t *)p;
+    p += align16((size_t)(n + 1) * 4);
+    int32_t *col = (int32_t *)p;
+    p += align16((size_t)nnz * 4);
+    int32_t *reach = nullptr, *ident = nullptr;
+    if (REACH) {
+      reach = (int32_t *)p;
+      p += align16((size_t)n * 4);
+    }
+    if (IDENT) {
+      ident = (int32_t *)p;
+      p += align16((size_t)n * 4);
+    }
+    double *acc = (double *)p;
+    p += align16((size_t)n * 8);
+    const int64_t r0 = g_row[c.row_off];
+    for (int v = tid; v <= n; v += SMALL_THREADS) row[v] = (int32_t)(g_row[c.row_off + v] - r0);
+    for (int e = tid; e < nnz; e += SMALL_THREADS) col[e] = g_col[r0 + e];
+    for (int v = tid; v < n; v += SMALL_THREADS) {
+      if (REACH) reach[v] = g_reach[c.vtx_off + v];
+      if (IDENT) ident[v] = g_ident[c.vtx_off + v];
+      acc[v] = 0.0;
+    }
+    __syncthreads();
+    const int ng = item.ngroups;
+    const int gsize = SMALL_THREADS / ng;
+    const int gid = tid / gsize;
+    Group g{tid % gsize, gsize, 1 + gid};
+    const size_t per = align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 2;
+    unsigned char *q = p + per * gid;
+    SrcState<FP32> st;
+    st.d = (int32_t *)q;
+    q += align16((size_t)n * 4);
+    st.queue = (int32_t *)q;
+    q += align16((size_t)n * 4);
+    st.sig = (double *)q;
+    q += align16((size_t)n * 8);
+    st.coef = (typename CoefT<FP32>::type *)q;
+    int32_t *lv = lvl_scratch + ((size_t)blockIdx.x * SMALL_MAX_GROUPS + gid) * (size_t)lvl_stride * 2;
+    st.lvl_start = lv;
+    st.lvl_exp = lv + lvl_stride;
+    st.qtail = &s_qtail[gid];
+    st.red = s_red[gid];
+    Weights wt{reach, ident};
+    for (int i = item.s_begin + gid; i < item.s_end; i += ng) {
+      const int32_t s = srcs ? (int32_t)srcs[i] : i;
+      bcreach_source<REACH, IDENT, FP32, true, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr);
+    }
+    __syncthreads();
+    for (int v = tid; v < n; v += SMALL_THREADS)
+      if (acc[v] != 0.0) atomicAdd(bcp + c.vtx_off + v, acc[v]);
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------- large path
+struct LargeSrc {
+  int32_t comp;
+  int32_t s;
+};
+
+// Per-CTA global scratch of the large path: each array holds grid * nmax
+// entries, CTA b owning [b * nmax, (b+1) * nmax) (lvl arrays: nmax + 2).
+struct LargeScratch {
+  int32_t *d;      // -1 between sources
+  int32_t *queue;
+  double *sig;     // 0 between sources
+  double *coef;    // 8 bytes per vertex in both precisions
+  double *acc;     // 0 between components
+  int32_t *lvl_start;
+  int32_t *lvl_exp;
+  int64_t nmax;
+};
+
+template <bool REACH, bool IDENT, bool FP32>
+__global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
+    const LargeSrc *__restrict__ work, int64_t nwork, unsigned long long *counter, const CompDesc *__restrict__ comps,
+    const int64_t *__restrict__ g_row, const int32_t *__restrict__ g_col, const int32_t *__restrict__ g_reach,
+    const int32_t *__restrict__ g_ident, double *bcp, LargeScratch sc, int *err, Debug dbg_in, int use_dbg) {
+  __shared__ unsigned long long s_idx;
+  __shared__ int s_qtail;
+  __shared__ double s_red[16];
+  const size_t b = blockIdx.x;
+  SrcState<FP32> st;
+  st.d = sc.d + b * sc.nmax;
+  st.queue = sc.queue + b * sc.nmax;
+  st.sig = sc.sig + b * sc.nmax;
+  st.coef = (typename CoefT<FP32>::type *)(sc.coef + b * sc.nmax);
+  double *acc = sc.acc + b * sc.nmax;
+  st.lvl_start = sc.lvl_start + b * (sc.nmax + 2);
+  st.lvl_exp = sc.lvl_exp + b * (sc.nmax + 2);
+  st.qtail = &s_qtail;
+  st.red = s_red;
+  Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+  int cur = -1;
+  for (;;) {
+    if (threadIdx.x == 0) s_idx = atomicAdd(counter, 1ull);
+    __syncthreads();
+    const unsigned long long idx = s_idx;
+    __syncthreads();
+    const int next = idx < (unsigned long long)nwork ? work[idx].comp : -1;
+    if (next != cur && cur >= 0) {  // flush the accumulator of the previous component
+      const CompDesc c = comps[cur];
+      for (int v = threadIdx.x; v < c.n; v += blockDim.x) {
+        if (acc[v] != 0.0) atomicAdd(bcp + c.vtx_off + v, acc[v]);
+        acc[v] = 0.0;
+      }
+      __syncthreads();
+    }
+    cur = next;
+    if (next < 0) break;
+    const CompDesc c = comps[cur];
+    Weights wt{REACH ? g_reach + c.vtx_off : nullptr, IDENT ? g_ident + c.vtx_off : nullptr};
+    bcreach_source<REACH, IDENT, FP32, false, true>(g, work[idx].s, c.n, g_row + c.row_off, g_col, wt, st, acc, c.fan,
+                                                    err, use_dbg ? &dbg_in : nullptr);
+  }
+}
+
+// bytes of global scratch per large-path CTA
+static size_t large_scratch_bytes(int64_t nmax) { return (size_t)nmax * (4 + 4 + 8 + 8 + 8) + (size_t)(nmax + 2) * 8; }
+
+// ---------------------------------------------------------- host side
+template <bool R, bool I, bool F>
+static int launch_small_t(Ctx &ctx, int grid, size_t smem, const SmallItem *items, int nitems, int *counter,
+                          const CompDesc *comps, const BcInput &in, const int64_t *srcs, int32_t *lvl, int lvl_stride,
+                          int *err) {
+  auto kern = k_bcreach_small<R, I, F>;
+  BCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<grid, SMALL_THREADS, smem, ctx.stream>>>(items, nitems, counter, comps, in.row, in.col, in.reach, in.ident,
+                                                 srcs, in.bcp, lvl, lvl_stride, err);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+template <bool R, bool I, bool F>
+static int launch_large_t(Ctx &ctx, int grid, const LargeSrc *work, int64_t nwork, unsigned long long *counter,
+                          const CompDesc *comps, const BcInput &in, const LargeScratch &sc, int *err,
+                          const Debug &dbg, int use_dbg) {
+  k_bcreach_large<R, I, F><<<grid, LARGE_THREADS, 0, ctx.stream>>>(work, nwork, counter, comps, in.row, in.col,
+                                                                  in.reach, in.ident, in.bcp, sc, err, dbg, use_dbg);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+#define BCS_DISPATCH3(FN, R, I, F, ...)                             \
+  ((R) ? ((I) ? ((F) ? FN<true, true, true>(__VA_ARGS__)            \
+                     : FN<true, true, false>(__VA_ARGS__))          \
+              : ((F) ? FN<true, false, true>(__VA_ARGS__)           \
+                     : FN<true, false, false>(__VA_ARGS__)))        \
+       : ((I) ? ((F) ? FN<false, true, true>(__VA_ARGS__)           \
+                     : FN<false, true, false>(__VA_ARGS__))         \
+              : ((F) ? FN<false, false, true>(__VA_ARGS__)          \
+                     : FN<false, false, false>(__VA_ARGS__))))
+
+// Shared memory given to each small-path CTA (two CTAs per SM).
+constexpr size_t SMALL_SMEM = 100 * 1024;
+
+int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po) {
+  const bool R = in.reach != nullptr, I = in.ident != nullptr, F = po.fp32_delta;
+  const bool dbg = po.dbg_d || po.dbg_sig || po.dbg_exp || po.dbg_delta;
+  const int64_t C = (int64_t)comps.size();
+  if (po.sources && C != 1) {
+    set_error("a source list needs exactly one component");
+    return BCS_EINVAL;
+  }
+  std::vector<SmallItem> items;
+  std::vector<LargeSrc> work;
+  int64_t nmax_large = 0, nmax_small = 0;
+  double total_small_cost = 0.0;
+  std::vector<int> ng_of(C, 0);
+  for (int64_t ci = 0; ci < C; ci++) {
+    const CompDesc &c = comps[ci];
+    if (c.n < 2) continue;
+    int ng = 0;
+    if (!po.force_large && !dbg) {
+      for (int cand = SMALL_MAX_GROUPS; cand >= 1; cand >>= 1)
+        if (small_smem_bytes(c.n, c.nnz, cand, R, I) <= SMALL_SMEM) {
+          ng = cand;
+          break;
+        }
+    }
+    ng_of[ci] = ng;
+    const int64_t ns = po.sources ? po.nsources : c.n;
+    if (ng) {
+      total_small_cost += (double)ns * (double)(c.nnz + c.n);
+      nmax_small = std::max<int64_t>(nmax_small, c.n);
+    } else {
+      nmax_large = std::max<int64_t>(nmax_large, c.n);
+    }
+  }
+  const int small_ctas = ctx.num_sms * 2;
+  const double target = total_small_cost / (double)(small_ctas * 8) + 1.0;
+  double work_se = 0.0;
+  for (int64_t ci = 0; ci < C; ci++) {
+    const CompDesc &c = comps[ci];
+    if (c.n < 2) continue;
+    const int64_t ns = po.sources ? po.nsources : c.n;
+    work_se += (double)ns * (double)c.nnz;
+    if (ng_of[ci]) {
+      const int ng = ng_of[ci];
+      const double per = (double)(c.nnz + c.n);
+      int64_t chunk = (int64_t)std::max(1.0, target / per);
+      chunk = ((chunk + ng - 1) / ng) * ng;
+      for (int64_t b = 0; b < ns; b += chunk)
+        items.push_back(SmallItem{(int32_t)ci, (int32_t)b, (int32_t)std::min<int64_t>(ns, b + chunk), ng});
+    } else {
+      for (int64_t i = 0; i < ns; i++)
+        work.push_back(LargeSrc{(int32_t)ci, (int32_t)(po.sources ? po.sources[i] : i)});
+    }
+  }
+  // biggest per-source cost first
+  std::stable_sort(items.begin(), items.end(), [&](const SmallItem &a, const SmallItem &b) {
+    return comps[a.comp].nnz + comps[a.comp].n > comps[b.comp].nnz + comps[b.comp].n;
+  });
+  ctx.stats.n_small_items = (int64_t)items.size();
+  ctx.stats.n_large_sources = (int64_t)work.size();
+  ctx.stats.work_sources_entries = work_se;
+  if (items.empty() && work.empty()) return BCS_OK;
+
+  DBuf<CompDesc> d_comps;
+  DBuf<int> d_err;
+  BCS_TRY(d_comps.alloc(C, ctx.stream));
+  BCS_TRY(d_err.alloc(4, ctx.stream));
+  BCS_CUDA(cudaMemcpyAsync(d_comps.p, comps.data(), C * sizeof(CompDesc), cudaMemcpyHostToDevice, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(d_err.p, 0, 4 * sizeof(int), ctx.stream));
+  DBuf<int64_t> d_srcs;
+  if (po.sources && !items.empty()) {
+    BCS_TRY(d_srcs.alloc(po.nsources, ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(d_srcs.p, po.sources, po.nsources * sizeof(int64_t), cudaMemcpyHostToDevice, ctx.stream));
+  }
+  if (!items.empty()) {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    DBuf<SmallItem> d_items;
+    DBuf<int32_t> lvl;
+    BCS_TRY(d_items.alloc(items.size(), ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(d_items.p, items.data(), items.size() * sizeof(SmallItem), cudaMemcpyHostToDevice,
+                             ctx.stream));
+    const int lvl_stride = (int)nmax_small + 2;
+    const int grid = std::min<int64_t>(small_ctas, (int64_t)items.size());
+    BCS_TRY(lvl.alloc((size_t)grid * SMALL_MAX_GROUPS * lvl_stride * 2, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(d_err.p + 1, 0, sizeof(int), ctx.stream));
+    BCS_TRY(BCS_DISPATCH3(launch_small_t, R, I, F, ctx, grid, SMALL_SMEM, d_items.p, (int)items.size(), d_err.p + 1,
+                          d_comps.p, in, po.sources ? d_srcs.p : nullptr, lvl.p, lvl_stride, d_err.p));
+    ctx.stats.ms_bcreach_small += tm.stop_ms();
+  }
+  if (!work.empty()) {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    DBuf<LargeSrc> d_work;
+    DBuf<unsigned long long> counter;
+    BCS_TRY(d_work.alloc(work.size(), ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(d_work.p, work.data(), work.size() * sizeof(LargeSrc), cudaMemcpyHostToDevice,
+                             ctx.stream));
+    BCS_TRY(counter.alloc(1, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), ctx.stream));
+    // CTAs: up to 3 per SM, fewer when the scratch would take more than half
+    // of the free device memory
+    size_t free_b = 0, total_b = 0;
+    BCS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    int64_t grid = (int64_t)ctx.num_sms * 3;
+    grid = std::min<int64_t>(grid, (int64_t)work.size());
+    const size_t per = large_scratch_bytes(nmax_large);
+    if ((size_t)grid * per > free_b / 2) grid = std::max<int64_t>(1, (int64_t)(free_b / 2 / per));
+    const size_t G = (size_t)grid, NM = (size_t)nmax_large;
+    DBuf<int32_t> sd, sq, sls, sle;
+    DBuf<double> ssig, scoef, sacc;
+    BCS_TRY(sd.alloc(G * NM, ctx.stream));
+    BCS_TRY(sq.alloc(G * NM, ctx.stream));
+    BCS_TRY(ssig.alloc(G * NM, ctx.stream));
+    BCS_TRY(scoef.alloc(G * NM, ctx.stream));
+    BCS_TRY(sacc.alloc(G * NM, ctx.stream));
+    BCS_TRY(sls.alloc(G * (NM + 2), ctx.stream));
+    BCS_TRY(sle.alloc(G * (NM + 2), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(sd.p, 0xFF, G * NM * sizeof(int32_t), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(ssig.p, 0, G * NM * sizeof(double), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(sacc.p, 0, G * NM * sizeof(double), ctx.stream));
+    LargeScratch sc{sd.p, sq.p, ssig.p, scoef.p, sacc.p, sls.p, sle.p, (int64_t)NM};
+    Debug dbgs{po.dbg_d, po.dbg_sig, po.dbg_exp, po.dbg_delta};
+    BCS_TRY(BCS_DISPATCH3(launch_large_t, R, I, F, ctx, (int)grid, d_work.p, (int64_t)work.size(), counter.p,
+                          d_comps.p, in, sc, d_err.p, dbgs, dbg ? 1 : 0));
+    ctx.stats.ms_bcreach_large += tm.stop_ms();
+  }
+  int h_err = 0;
+  BCS_CUDA(cudaMemcpyAsync(&h_err, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  if (h_err & ERR_OVERFLOW) {
+    set_error("shortest-path counts overflowed the FP64 range within one BFS level");
+    return BCS_EOVERFLOW;
+  }
+  return BCS_OK;
+}
+
+}  // namespace bcs

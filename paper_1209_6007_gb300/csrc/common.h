@@ -1,0 +1,190 @@
+// common.h - internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/bcshatter.h"
+
+namespace bcs {
+
+// ------------------------------------------------------------------ errors
+void set_error(const std::string &msg);
+const std::string &get_error();
+
+struct Status {
+  int code = BCS_OK;
+  bool ok() const { return code == BCS_OK; }
+};
+
+#define BCS_CUDA(expr)                                                                   \
+  do {                                                                                   \
+    cudaError_t e_ = (expr);                                                             \
+    if (e_ != cudaSuccess) {                                                             \
+      ::bcs::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));              \
+      return (e_ == cudaErrorMemoryAllocation) ? BCS_ENOMEM : BCS_ECUDA;                 \
+    }                                                                                    \
+  } while (0)
+
+#define BCS_TRY(expr)        \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != BCS_OK) return rc_; \
+  } while (0)
+
+// ------------------------------------------------------- device buffers
+// Stream-ordered device allocation from the device's default memory pool
+// (its release threshold is raised once per device so freed blocks stay
+// cached between calls).
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  cudaStream_t s = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFreeAsync(p, s);
+    p = nullptr;
+    n = 0;
+  }
+  int alloc(size_t count, cudaStream_t stream) {
+    release();
+    s = stream;
+    n = count;
+    size_t bytes = (count > 0 ? count : 1) * sizeof(T);
+    cudaError_t e = cudaMallocAsync((void **)&p, bytes, stream);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      set_error(std::string("cudaMallocAsync(") + std::to_string(bytes) + " B): " + cudaGetErrorString(e));
+      return BCS_ENOMEM;
+    }
+    return BCS_OK;
+  }
+};
+
+// ------------------------------------------------------- call context
+struct Ctx {
+  int device = 0;
+  int num_sms = 0;
+  size_t smem_optin = 0;
+  cudaStream_t stream = 0;
+  bcs_stats stats{};
+  bool timing = true;
+  int64_t launches = 0;
+};
+
+int make_ctx(const bcs_opts *opts, Ctx *ctx);
+
+// CUDA-event stopwatch on the call's stream.
+struct StageTimer {
+  cudaEvent_t a = nullptr, b = nullptr;
+  cudaStream_t s = 0;
+  StageTimer(cudaStream_t stream);
+  ~StageTimer();
+  void start();
+  double stop_ms();  // synchronises on the stop event
+};
+
+// ------------------------------------------------------- graph on device
+struct DevGraph {
+  int64_t n = 0, nnz = 0;
+  const int64_t *rp = nullptr;
+  const int32_t *col = nullptr;
+};
+
+// Pieces (components of the shattered graph) before identical merging:
+// slots are (piece, original vertex) pairs, contiguous per piece, ascending
+// by original id inside a piece; scol holds global slot ids.
+struct HostPieces {
+  std::vector<int64_t> piece_off;  // npieces+1 (slot offsets)
+  std::vector<int64_t> piece_N;    // npieces
+  std::vector<int32_t> slot_org;   // nslots
+  std::vector<int32_t> slot_reach; // nslots
+  std::vector<int32_t> slot_piece; // nslots
+  std::vector<int64_t> srow;       // nslots+1
+  std::vector<int32_t> scol;       // entries (global slot ids)
+  int64_t npieces() const { return (int64_t)piece_off.size() - 1; }
+  int64_t nslots() const { return (int64_t)slot_org.size(); }
+};
+
+// Build the pieces on the host from the graph left by degree-1 removal.
+// alive[v]: vertex still present; reach[v]: its reach; ccN[v]: size of its
+// connected component in the input; cclab[v]: component label.
+int host_build_pieces(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *alive,
+                      const int32_t *reach, const int64_t *ccN, const int32_t *cclab, bool articulation,
+                      HostPieces *out);
+
+// Pieces after identical merging, on the device.
+struct DevMerged {
+  int64_t npieces = 0, nmerged = 0, nentries = 0, nslots = 0;
+  DBuf<int64_t> piece_off;   // npieces+1 (merged vertex offsets)
+  DBuf<int64_t> piece_N;     // npieces
+  DBuf<int64_t> mrow;        // nmerged+1
+  DBuf<int32_t> mcol;        // nentries (local ids)
+  DBuf<int32_t> morg;        // nmerged
+  DBuf<int32_t> mreach;      // nmerged
+  DBuf<int32_t> mident;      // nmerged
+  DBuf<double> mcorr;        // nmerged
+  DBuf<int32_t> slot_org;    // nslots (pre-merge)
+  DBuf<int32_t> slot_to_m;   // nslots -> merged vertex
+  std::vector<int64_t> h_piece_off;  // host copies for planning
+  std::vector<int64_t> h_piece_ent;  // entries per piece
+  int32_t max_ident = 1;
+};
+
+int device_merge(Ctx &ctx, const HostPieces &hp, bool identical, DevMerged *out);
+
+// ------------------------------------------------------- graph kernels
+int launch_validate(Ctx &ctx, const DevGraph &g, int *d_flags);
+int launch_cc(Ctx &ctx, const DevGraph &g, int32_t *d_label, int64_t *d_N);
+int run_peel(Ctx &ctx, const DevGraph &g, const int64_t *d_N, uint8_t *d_alive, int32_t *d_reach,
+             int64_t *d_bcpre);
+int launch_bc_init(Ctx &ctx, int64_t n, const int64_t *d_bcpre, double *d_bc);
+int launch_mapback(Ctx &ctx, int64_t nslots, const int32_t *slot_org, const int32_t *slot_to_m,
+                   const double *bcp, double *d_bc);
+int launch_fill_i32(Ctx &ctx, int32_t *p, int64_t n, int32_t v);
+int launch_exclusive_scan(Ctx &ctx, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total);
+
+// ------------------------------------------------------- Bc-Reach
+// One component handed to the Bc-Reach kernels.
+struct CompDesc {
+  int64_t vtx_off;  // first vertex (global index into reach/ident/bcp arrays)
+  int64_t row_off;  // pointer to row offsets: row[vtx_off .. vtx_off+n]
+  int32_t n;        // vertices
+  int32_t maxdeg;   // largest degree
+  int64_t nnz;      // CSR entries
+  double fan;       // bound on sigma growth per level (max over v of sum of
+                    // ident over its neighbours)
+};
+
+struct BcInput {
+  const int64_t *row = nullptr;   // global row offsets (indexed by vertex)
+  const int32_t *col = nullptr;   // local neighbour ids
+  const int32_t *reach = nullptr; // nullable (all 1)
+  const int32_t *ident = nullptr; // nullable (all 1)
+  double *bcp = nullptr;          // accumulation target, indexed by vertex
+};
+
+struct BcPlanOpts {
+  bool fp32_delta = false;
+  const int64_t *sources = nullptr;  // host; nullable = every vertex
+  int64_t nsources = 0;
+  bool force_large = false;           // route every piece through the global path
+  // debug output for a single source (large path only)
+  int32_t *dbg_d = nullptr;
+  double *dbg_sig = nullptr;
+  int32_t *dbg_exp = nullptr;
+  double *dbg_delta = nullptr;
+};
+
+// Plan and run Bc-Reach over the given components.  comps are host
+// descriptors; their vertex ranges index BcInput's arrays.
+int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po);
+
+}  // namespace bcs

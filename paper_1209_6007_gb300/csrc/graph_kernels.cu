@@ -1,0 +1,416 @@
+// graph_kernels.cu - whole-graph kernels: CSR check, connected components,
+// degree-1 removal rounds, prefix sums, bc initialisation and map-back.
+#include <algorithm>
+#include <mutex>
+
+#include "common.h"
+
+namespace bcs {
+
+static inline int grid_for(int64_t work, int block, int max_blocks) {
+  int64_t b = (work + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+// Pinned 8-byte scratch per host thread for small device->host reads.
+static int64_t *pinned_scalar() {
+  static thread_local int64_t *p = nullptr;
+  if (!p) {
+    if (cudaMallocHost((void **)&p, 4 * sizeof(int64_t)) != cudaSuccess) p = nullptr;
+  }
+  return p;
+}
+
+static int read_scalar(Ctx &ctx, const int64_t *d_src, int64_t *out) {
+  int64_t *h = pinned_scalar();
+  if (!h) {
+    set_error("cudaMallocHost of a pinned scalar failed");
+    return BCS_ENOMEM;
+  }
+  BCS_CUDA(cudaMemcpyAsync(h, d_src, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  *out = *h;
+  return BCS_OK;
+}
+
+// ---------------------------------------------------------------- validate
+// Warp per row: bounds, self-loops, strictly ascending rows (no duplicates)
+// and symmetry (binary search of u in the row of each neighbour).
+// flags: 1 range/offsets, 2 self-loop, 4 unsorted/duplicate, 8 asymmetric.
+__global__ void k_validate(int64_t n, int64_t nnz, const int64_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, int *flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  int f = 0;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int64_t b = rp[u], e = rp[u + 1];
+    if (b < 0 || b > e || e > nnz || (u == 0 && b != 0) || (u == n - 1 && e != nnz)) {
+      f |= 1;
+      continue;
+    }
+    for (int64_t k = b + lane; k < e; k += 32) {
+      const int32_t v = col[k];
+      if (v < 0 || v >= n) {
+        f |= 1;
+        continue;
+      }
+      if (v == u) f |= 2;
+      if (k > b && col[k - 1] >= v) f |= 4;
+      int64_t lo = rp[v], hi = rp[v + 1];
+      if (lo < 0 || hi > nnz || lo > hi) {
+        f |= 1;
+        continue;
+      }
+      const int64_t end = hi;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (col[mid] < (int32_t)u) lo = mid + 1;
+        else hi = mid;
+      }
+      if (lo >= end || col[lo] != (int32_t)u) f |= 8;
+    }
+  }
+  f = __reduce_or_sync(0xffffffffu, f);
+  if (lane == 0 && f) atomicOr(flags, f);
+}
+
+int launch_validate(Ctx &ctx, const DevGraph &g, int *d_flags) {
+  BCS_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int), ctx.stream));
+  if (g.n == 0) return BCS_OK;
+  int block = 256;
+  int grid = grid_for(g.n * 32, block, ctx.num_sms * 16);
+  k_validate<<<grid, block, 0, ctx.stream>>>(g.n, g.nnz, g.rp, g.col, d_flags);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+// ---------------------------------------------------- connected components
+// Union-find with hooking of the larger root under the smaller one (so
+// every parent pointer decreases and the root is the smallest id) and path
+// halving in find.
+__device__ __forceinline__ int32_t vload(const int32_t *p) { return *(volatile const int32_t *)p; }
+
+__device__ int32_t uf_find(int32_t *p, int32_t x) {
+  for (;;) {
+    int32_t px = vload(p + x);
+    if (px == x) return x;
+    int32_t gpx = vload(p + px);
+    if (gpx == px) return px;
+    *(volatile int32_t *)(p + x) = gpx;
+    x = gpx;
+  }
+}
+
+__device__ void uf_unite(int32_t *p, int32_t a, int32_t b) {
+  for (;;) {
+    a = uf_find(p, a);
+    b = uf_find(p, b);
+    if (a == b) return;
+    if (a < b) {
+      int32_t t = a;
+      a = b;
+      b = t;
+    }
+    if (atomicCAS(p + a, a, b) == a) return;
+  }
+}
+
+__global__ void k_iota(int64_t n, int32_t *p) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    p[v] = (int32_t)v;
+}
+
+__global__ void k_cc_hook(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                          int32_t *parent) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t u = warp; u < n; u += nwarps) {
+    const int64_t b = rp[u], e = rp[u + 1];
+    for (int64_t k = b + lane; k < e; k += 32) {
+      const int32_t v = col[k];
+      if (v > u) uf_unite(parent, (int32_t)u, v);
+    }
+  }
+}
+
+__global__ void k_cc_finish(int64_t n, int32_t *parent, unsigned long long *cnt) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t r = uf_find(parent, (int32_t)v);
+    parent[v] = r;
+    atomicAdd(cnt + r, 1ull);
+  }
+}
+
+__global__ void k_cc_size(int64_t n, const int32_t *__restrict__ label, const int64_t *__restrict__ cnt,
+                          int64_t *N) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    N[v] = cnt[label[v]];
+}
+
+int launch_cc(Ctx &ctx, const DevGraph &g, int32_t *d_label, int64_t *d_N) {
+  if (g.n == 0) return BCS_OK;
+  DBuf<int64_t> cnt;
+  BCS_TRY(cnt.alloc(g.n, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(cnt.p, 0, g.n * sizeof(int64_t), ctx.stream));
+  int block = 256;
+  int gv = grid_for(g.n, block, ctx.num_sms * 32);
+  k_iota<<<gv, block, 0, ctx.stream>>>(g.n, d_label);
+  int gw = grid_for(g.n * 32, block, ctx.num_sms * 16);
+  k_cc_hook<<<gw, block, 0, ctx.stream>>>(g.n, g.rp, g.col, d_label);
+  k_cc_finish<<<gv, block, 0, ctx.stream>>>(g.n, d_label, (unsigned long long *)cnt.p);
+  k_cc_size<<<gv, block, 0, ctx.stream>>>(g.n, d_label, cnt.p, d_N);
+  ctx.launches += 4;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+// ------------------------------------------------------ degree-1 removal
+// Section 3.3.1.  Leaves are removed in rounds: every vertex of live degree
+// 1 at the start of a round is removed in that round, except that of two
+// adjacent leaves (a component reduced to one edge) only the larger id is
+// removed, into the smaller.  For a removed leaf u with neighbour v,
+// r = reach[u] and N = |C| (the sum of reach over C never changes):
+//   bc[u] += (r - 1)(N - r),  bc[v] += r (N - r - 1),  reach[v] += r.
+// These terms depend only on u's own reach, which no other removal of the
+// same round touches, so the leaves of a round are independent.
+__device__ __forceinline__ void push_warp_aggregated(int32_t *queue, unsigned long long *count, int32_t v) {
+  unsigned mask = __activemask();
+  int leader = __ffs(mask) - 1;
+  int lane = threadIdx.x & 31;
+  int rank = __popc(mask & ((1u << lane) - 1));
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  queue[base + rank] = v;
+}
+
+__global__ void k_peel_init(int64_t n, const int64_t *__restrict__ rp, int32_t *deg, int32_t *reach,
+                            uint8_t *alive, int64_t *bcpre, int32_t *frontier, unsigned long long *fcount) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    int32_t d = (int32_t)(rp[v + 1] - rp[v]);
+    deg[v] = d;
+    reach[v] = 1;
+    alive[v] = 1;
+    bcpre[v] = 0;
+    if (d == 1) push_warp_aggregated(frontier, fcount, (int32_t)v);
+  }
+}
+
+// target[i] = the neighbour the i-th frontier vertex is removed into, or -1
+__global__ void k_peel_decide(int64_t fcount, const int32_t *__restrict__ frontier, const int64_t *__restrict__ rp,
+                              const int32_t *__restrict__ col, const int32_t *__restrict__ deg,
+                              const uint8_t *__restrict__ alive, int32_t *target) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t u = frontier[i];
+    int32_t t = -1;
+    if (alive[u] && deg[u] == 1) {
+      int32_t v = -1;
+      for (int64_t k = rp[u]; k < rp[u + 1]; k++) {
+        if (alive[col[k]]) {
+          v = col[k];
+          break;
+        }
+      }
+      if (v >= 0 && !(deg[v] == 1 && u < v)) t = v;
+    }
+    target[i] = t;
+  }
+}
+
+__global__ void k_peel_apply(int64_t fcount, const int32_t *__restrict__ frontier, const int32_t *__restrict__ target,
+                             const int64_t *__restrict__ N, int32_t *deg, int32_t *reach, uint8_t *alive,
+                             int64_t *bcpre, int32_t *next, unsigned long long *ncount) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t v = target[i];
+    if (v < 0) continue;
+    const int32_t u = frontier[i];
+    const int64_t r = reach[u];
+    const int64_t nc = N[u];
+    atomicAdd((unsigned long long *)(bcpre + u), (unsigned long long)((r - 1) * (nc - r)));
+    atomicAdd((unsigned long long *)(bcpre + v), (unsigned long long)(r * (nc - r - 1)));
+    atomicAdd(reach + v, (int32_t)r);
+    alive[u] = 0;
+    deg[u] = 0;
+    if (atomicSub(deg + v, 1) == 2) push_warp_aggregated(next, ncount, v);
+  }
+}
+
+int run_peel(Ctx &ctx, const DevGraph &g, const int64_t *d_N, uint8_t *d_alive, int32_t *d_reach,
+             int64_t *d_bcpre) {
+  if (g.n == 0) return BCS_OK;
+  DBuf<int32_t> deg, fa, fb, target;
+  DBuf<int64_t> counts;
+  BCS_TRY(deg.alloc(g.n, ctx.stream));
+  BCS_TRY(fa.alloc(g.n, ctx.stream));
+  BCS_TRY(fb.alloc(g.n, ctx.stream));
+  BCS_TRY(target.alloc(g.n, ctx.stream));
+  BCS_TRY(counts.alloc(2, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(counts.p, 0, 2 * sizeof(int64_t), ctx.stream));
+  int block = 256;
+  int gv = grid_for(g.n, block, ctx.num_sms * 32);
+  k_peel_init<<<gv, block, 0, ctx.stream>>>(g.n, g.rp, deg.p, d_reach, d_alive, d_bcpre, fa.p,
+                                            (unsigned long long *)counts.p);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  int64_t fcount = 0;
+  BCS_TRY(read_scalar(ctx, counts.p, &fcount));
+  int32_t *cur = fa.p, *nxt = fb.p;
+  int cur_slot = 0;
+  int64_t rounds = 0;
+  while (fcount > 0) {
+    int nxt_slot = 1 - cur_slot;
+    BCS_CUDA(cudaMemsetAsync(counts.p + nxt_slot, 0, sizeof(int64_t), ctx.stream));
+    int gf = grid_for(fcount, block, ctx.num_sms * 32);
+    k_peel_decide<<<gf, block, 0, ctx.stream>>>(fcount, cur, g.rp, g.col, deg.p, d_alive, target.p);
+    k_peel_apply<<<gf, block, 0, ctx.stream>>>(fcount, cur, target.p, d_N, deg.p, d_reach, d_alive, d_bcpre, nxt,
+                                               (unsigned long long *)(counts.p + nxt_slot));
+    ctx.launches += 2;
+    BCS_CUDA(cudaGetLastError());
+    BCS_TRY(read_scalar(ctx, counts.p + nxt_slot, &fcount));
+    std::swap(cur, nxt);
+    cur_slot = nxt_slot;
+    rounds++;
+  }
+  ctx.stats.peel_rounds = rounds;
+  return BCS_OK;
+}
+
+// ------------------------------------------------------------ bc helpers
+__global__ void k_bc_init(int64_t n, const int64_t *__restrict__ bcpre, double *bc) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    bc[v] = bcpre ? (double)bcpre[v] : 0.0;
+}
+
+int launch_bc_init(Ctx &ctx, int64_t n, const int64_t *d_bcpre, double *d_bc) {
+  if (n == 0) return BCS_OK;
+  k_bc_init<<<grid_for(n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(n, d_bcpre, d_bc);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+// Eq. 5: bc[v] += bc'[v'] for every copy v' of v (a merged vertex stands for
+// each of its members, so every pre-merge slot reads its merged vertex).
+__global__ void k_mapback(int64_t nslots, const int32_t *__restrict__ slot_org, const int32_t *__restrict__ slot_to_m,
+                          const double *__restrict__ bcp, double *bc) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nslots; p += (int64_t)gridDim.x * blockDim.x) {
+    double x = bcp[slot_to_m[p]];
+    if (x != 0.0) atomicAdd(bc + slot_org[p], x);
+  }
+}
+
+int launch_mapback(Ctx &ctx, int64_t nslots, const int32_t *slot_org, const int32_t *slot_to_m, const double *bcp,
+                   double *d_bc) {
+  if (nslots == 0) return BCS_OK;
+  k_mapback<<<grid_for(nslots, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(nslots, slot_org, slot_to_m, bcp, d_bc);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+__global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+int launch_fill_i32(Ctx &ctx, int32_t *p, int64_t n, int32_t v) {
+  if (n == 0) return BCS_OK;
+  k_fill_i32<<<grid_for(n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(p, n, v);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+// ------------------------------------------------------------ prefix sum
+// Exclusive scan of int64: each block scans SCAN_TILE elements and writes
+// its total; the totals are scanned recursively and added back.
+constexpr int SCAN_BLOCK = 512;
+constexpr int SCAN_ITEMS = 4;
+constexpr int SCAN_TILE = SCAN_BLOCK * SCAN_ITEMS;
+
+__device__ __forceinline__ int64_t block_exclusive_scan(int64_t x, int64_t *warp_sums, int64_t *total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int64_t inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int64_t y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) warp_sums[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    int64_t w = lane < (SCAN_BLOCK / 32) ? warp_sums[lane] : 0;
+    int64_t wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int64_t y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < (SCAN_BLOCK / 32)) warp_sums[lane] = wi - w;
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  int64_t r = inc - x + warp_sums[wid];
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_tiles(const int64_t *__restrict__ in, int64_t *out, int64_t n, int64_t *tile_sums) {
+  __shared__ int64_t warp_sums[SCAN_BLOCK / 32];
+  __shared__ int64_t total;
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+  int64_t v[SCAN_ITEMS];
+  int64_t s = 0;
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; i++) {
+    v[i] = (base + i < n) ? in[base + i] : 0;
+    s += v[i];
+  }
+  int64_t off = block_exclusive_scan(s, warp_sums, &total);
+#pragma unroll
+  for (int i = 0; i < SCAN_ITEMS; i++) {
+    if (base + i < n) out[base + i] = off;
+    off += v[i];
+  }
+  if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+__global__ void k_scan_add(int64_t *out, int64_t n, const int64_t *__restrict__ tile_off) {
+  const int64_t base = (int64_t)blockIdx.x * SCAN_TILE;
+  const int64_t add = tile_off[blockIdx.x];
+  for (int i = threadIdx.x; i < SCAN_TILE; i += blockDim.x)
+    if (base + i < n) out[base + i] += add;
+}
+
+int launch_exclusive_scan(Ctx &ctx, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total) {
+  if (n == 0) {
+    BCS_CUDA(cudaMemsetAsync(d_total, 0, sizeof(int64_t), ctx.stream));
+    return BCS_OK;
+  }
+  int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+  if (tiles > INT32_MAX) {
+    set_error("scan too large");
+    return BCS_EINVAL;
+  }
+  DBuf<int64_t> sums, sums_off;
+  BCS_TRY(sums.alloc(tiles, ctx.stream));
+  BCS_TRY(sums_off.alloc(tiles, ctx.stream));
+  k_scan_tiles<<<(unsigned)tiles, SCAN_BLOCK, 0, ctx.stream>>>(in, out, n, sums.p);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  if (tiles == 1) {
+    BCS_CUDA(cudaMemcpyAsync(d_total, sums.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx.stream));
+    return BCS_OK;
+  }
+  BCS_TRY(launch_exclusive_scan(ctx, sums.p, sums_off.p, tiles, d_total));
+  k_scan_add<<<(unsigned)tiles, SCAN_BLOCK, 0, ctx.stream>>>(out, n, sums_off.p);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+}  // namespace bcs

@@ -1,0 +1,198 @@
+"""GPU path against the oracle, through the C ABI (needs a CUDA device).
+
+Bars (from the arithmetic of each side):
+* distances, path counts below 2^53, the partition, reach and ident:
+  bit-exact;
+* bc in FP64: max|gpu - oracle| <= 1e-12 * max|oracle|;
+* bc with the FP32 dependency recurrence: <= 1e-5 * max|oracle|.
+"""
+import numpy as np
+import pytest
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-12
+TOL32 = 1e-5
+ALL = oracle.STEP_D | oracle.STEP_A | oracle.STEP_I
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    if a.size == 0:
+        return 0.0
+    return float(np.max(np.abs(a - b))) / max(1.0, float(np.max(np.abs(b))))
+
+
+def on_device(g):
+    import torch
+    return torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda()
+
+
+def families():
+    out = [gg.path(2), gg.path(3), gg.path(40), gg.star(6), gg.cycle(9), gg.cycle(10), gg.complete(7),
+           gg.complete_bipartite(3, 5), gg.grid(12, 9), gg.random_tree(60, 3)]
+    for seed in range(6):
+        base = gg.gnp(30 + 7 * seed, 0.08 + 0.02 * seed, seed)
+        out.append(gg.with_twins_and_pendants(base, seed, 4, 10, 2))
+    out.append(gg.disjoint_union(gg.cycle(5), gg.path(4), gg.complete(4), gg.star(5), gg.gnp(1, 0.5, 0)))
+    out.append(gg.from_edges(5, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4)]))  # C4 + pendant
+    out.append(gg.config(1, scale_pct=10))
+    return out
+
+
+FAMILIES = families()
+
+
+# ----------------------------------------------------------- single source
+@pytest.mark.parametrize("s", [0, 7, 1234, 2599])
+def test_sssp_bit_exact_config1(gpu, s):
+    g = gg.config(1)
+    ref = oracle.sssp(g, s)
+    got = gpu.debug_sssp(g.row_ptr, g.col, s)
+    assert np.array_equal(got.d, ref.d)
+    reach = ref.d >= 0
+    sig_ref = ref.sigma_float()
+    sig_got = np.ldexp(got.sig_m, got.sig_e)
+    assert np.all(sig_ref[reach] < 2.0 ** 53)
+    assert np.array_equal(sig_got[reach], sig_ref[reach])
+    assert np.all(got.sig_m[~reach] == 0)
+    assert rel(got.delta, ref.delta) <= TOL64
+
+
+def test_sssp_grid_beyond_double_range(gpu):
+    """Path counts up to C(1398, 699) ~ 2^1392: the per-level exponent keeps them."""
+    side = 700
+    g = gg.grid(side, side)
+    ref = oracle.sssp(g, 0)
+    got = gpu.debug_sssp(g.row_ptr, g.col, 0)
+    assert np.array_equal(got.d, ref.d)
+    # compare sigma as (log2) magnitudes: m * 2^e on both sides
+    lr = np.log2(ref.sig_m) + ref.sig_e
+    lg = np.log2(got.sig_m) + got.sig_e
+    assert np.max(np.abs(lr - lg)) < 1e-9
+    small = ref.sig_e < 53
+    assert np.array_equal(np.ldexp(got.sig_m[small], got.sig_e[small]), np.ldexp(ref.sig_m[small], ref.sig_e[small].astype(np.int32)))
+    assert int(got.sig_e[-1]) > 1024
+    assert rel(got.delta, ref.delta) <= TOL64
+    got32 = gpu.debug_sssp(g.row_ptr, g.col, 0, delta_fp32=True)
+    assert rel(got32.delta, ref.delta) <= TOL32
+
+
+# ------------------------------------------------------------- plain
+@pytest.mark.parametrize("g", FAMILIES, ids=lambda g: g.name)
+def test_plain_families(gpu, g):
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_plain(g.row_ptr, g.col), ref) <= TOL64
+    assert rel(gpu.bc_plain(g.row_ptr, g.col, delta_fp32=True), ref) <= TOL32
+
+
+def test_plain_config1_host_and_device(gpu):
+    g = gg.config(1)
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_plain(g.row_ptr, g.col), ref) <= TOL64
+    rp, col = on_device(g)
+    got = gpu.bc_plain(rp, col)
+    assert got.is_cuda
+    assert rel(got.cpu().numpy(), ref) <= TOL64
+    assert rel(gpu.bc_plain(rp, col, delta_fp32=True).cpu().numpy(), ref) <= TOL32
+
+
+# ------------------------------------------------------------- shattered
+@pytest.mark.parametrize("steps", [0, 1, 2, 3, 4, 5, 6, 7])
+@pytest.mark.parametrize("g", FAMILIES, ids=lambda g: g.name)
+def test_shattered_families(gpu, g, steps):
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, steps=steps), ref) <= TOL64
+
+
+@pytest.mark.parametrize("steps", [1, 3, 7])
+def test_shattered_config1(gpu, steps):
+    g = gg.config(1)
+    ref = oracle.bc(g)
+    rp, col = on_device(g)
+    assert rel(gpu.bc_shattered(rp, col, steps=steps).cpu().numpy(), ref) <= TOL64
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, steps=steps, delta_fp32=True), ref) <= TOL32
+
+
+def test_shattered_articulation_scaled(gpu):
+    """Config 2 at 5% of its blocks: full oracle in seconds, many pieces."""
+    g = gg.config(2, scale_pct=5)
+    ref = oracle.bc(g)
+    got = gpu.bc_shattered(g.row_ptr, g.col)
+    assert rel(got, ref) <= TOL64
+    st = gpu.last_stats()
+    assert st["n_pieces"] > 100
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, delta_fp32=True), ref) <= TOL32
+
+
+# ------------------------------------------------------------ partition
+def canon_gpu(c):
+    out = {}
+    for p in range(c.n_pieces):
+        reach, classes = {}, []
+        for m in range(int(c.piece_vtx_off[p]), int(c.piece_vtx_off[p + 1])):
+            mem = [int(x) for x in c.members_of(m)]
+            assert int(c.ident[m]) == len(mem)
+            assert int(c.org[m]) == min(mem)
+            for x in mem:
+                reach[x] = int(c.reach[m])
+            if len(mem) >= 2:
+                classes.append(tuple(sorted(mem)))
+        out[tuple(sorted(reach))] = (reach, sorted(classes), int(c.piece_N[p]))
+    return out
+
+
+def canon_oracle(pieces):
+    return {p.vertices: (dict(p.reach), sorted(p.classes), p.N) for p in pieces}
+
+
+@pytest.mark.parametrize("steps", [0, 1, 2, 3, 4, 5, 6, 7])
+def test_partition_bit_exact(gpu, steps):
+    for g in [gg.config(1), gg.config(2, scale_pct=2), gg.complete_bipartite(3, 4), gg.complete(5),
+              gg.with_twins_and_pendants(gg.gnp(40, 0.1, 9), 9, 6, 8, 3)]:
+        got = canon_gpu(gpu.shatter(g.row_ptr, g.col, steps=steps))
+        ref = canon_oracle(oracle.shatter(g, steps))
+        assert got == ref, g.name
+
+
+# --------------------------------------------- full size, sampled sources
+def test_articulation_full_size_sources_vs_oracle(gpu):
+    """Config 2 at full size: plain Brandes on 256 seeded sources against the
+    oracle's partial sums (Eq. 2)."""
+    g = gg.config(2)
+    rng = np.random.default_rng(0xB0C00002)
+    src = rng.choice(g.n, size=256, replace=False)
+    ref = oracle.bc_sources(g, src)
+    got = gpu.bc_sources(g.row_ptr, g.col, src)
+    assert rel(got, ref) <= TOL64
+
+
+# --------------------------------------------------------------- errors
+def test_malformed_inputs_rejected(gpu):
+    bad = {
+        "asymmetric": (np.array([0, 1, 1], np.int64), np.array([1], np.int32)),
+        "self-loop": (np.array([0, 1, 2], np.int64), np.array([0, 1], np.int32)),
+        "duplicate": (np.array([0, 2, 4], np.int64), np.array([1, 1, 0, 0], np.int32)),
+        "unsorted": (np.array([0, 2, 3, 4], np.int64), np.array([2, 1, 0, 0], np.int32)),
+        "out-of-range": (np.array([0, 1, 2], np.int64), np.array([5, 0], np.int32)),
+    }
+    for name, (rp, col) in bad.items():
+        for fn in (gpu.bc_plain, gpu.bc_shattered):
+            with pytest.raises(gpu.BcsError) as e:
+                fn(rp, col)
+            assert e.value.code == gpu._lib.BCS_EINVAL, name
+
+
+def test_degenerate_graphs(gpu):
+    one = (np.array([0, 0], np.int64), np.zeros(0, np.int32))
+    assert np.array_equal(gpu.bc_plain(*one), [0.0])
+    assert np.array_equal(gpu.bc_shattered(*one), [0.0])
+    empty5 = (np.zeros(6, np.int64), np.zeros(0, np.int32))
+    assert np.array_equal(gpu.bc_shattered(*empty5), np.zeros(5))
+    k2 = gg.path(2)
+    assert np.array_equal(gpu.bc_shattered(k2.row_ptr, k2.col), [0.0, 0.0])
+    assert gpu.shatter(k2.row_ptr, k2.col).n_pieces == 0
