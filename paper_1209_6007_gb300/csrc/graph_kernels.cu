@@ -138,10 +138,12 @@ __global__ void k_cc_hook(int64_t n, const int64_t *__restrict__ rp, const int32
   }
 }
 
-__global__ void k_cc_finish(int64_t n, int32_t *parent, unsigned long long *cnt) {
+// Roots go to a separate array: the path-halving writes of concurrent finds
+// only ever touch `parent`, so a written label is never overwritten.
+__global__ void k_cc_finish(int64_t n, int32_t *parent, int32_t *label, unsigned long long *cnt) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
     int32_t r = uf_find(parent, (int32_t)v);
-    parent[v] = r;
+    label[v] = r;
     atomicAdd(cnt + r, 1ull);
   }
 }
@@ -155,14 +157,16 @@ __global__ void k_cc_size(int64_t n, const int32_t *__restrict__ label, const in
 int launch_cc(Ctx &ctx, const DevGraph &g, int32_t *d_label, int64_t *d_N) {
   if (g.n == 0) return BCS_OK;
   DBuf<int64_t> cnt;
+  DBuf<int32_t> parent;
   BCS_TRY(cnt.alloc(g.n, ctx.stream));
+  BCS_TRY(parent.alloc(g.n, ctx.stream));
   BCS_CUDA(cudaMemsetAsync(cnt.p, 0, g.n * sizeof(int64_t), ctx.stream));
   int block = 256;
   int gv = grid_for(g.n, block, ctx.num_sms * 32);
-  k_iota<<<gv, block, 0, ctx.stream>>>(g.n, d_label);
+  k_iota<<<gv, block, 0, ctx.stream>>>(g.n, parent.p);
   int gw = grid_for(g.n * 32, block, ctx.num_sms * 16);
-  k_cc_hook<<<gw, block, 0, ctx.stream>>>(g.n, g.rp, g.col, d_label);
-  k_cc_finish<<<gv, block, 0, ctx.stream>>>(g.n, d_label, (unsigned long long *)cnt.p);
+  k_cc_hook<<<gw, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p);
+  k_cc_finish<<<gv, block, 0, ctx.stream>>>(g.n, parent.p, d_label, (unsigned long long *)cnt.p);
   k_cc_size<<<gv, block, 0, ctx.stream>>>(g.n, d_label, cnt.p, d_N);
   ctx.launches += 4;
   BCS_CUDA(cudaGetLastError());
