@@ -137,6 +137,30 @@ int bcs_bc_sources(const bcs_csr *csr, const int64_t *src, int64_t k, const bcs_
 int bcs_debug_sssp(const bcs_csr *csr, int64_t s, const bcs_opts *opts, int32_t *d,
                    double *sigma_mant, int32_t *sigma_exp2, double *delta);
 
+/* Largest graph bcs_bc_plain_noalloc accepts (vertices). */
+#define BCS_NOALLOC_MAX_N 16384
+
+/*
+ * Plain Brandes, as bcs_bc_plain, without allocating any device memory.
+ * The paper has no counterpart: this variant exists for callers that cannot
+ * let a library allocate on the GPU, such as a serving process that gives
+ * nearly all device memory to its own pool at start-up, or a latency-critical
+ * loop that must never enter the CUDA allocator.
+ *
+ * Arguments: csr->on_device must be 1 (row_ptr, col and bc_out are device
+ * pointers on the selected device); csr->n <= BCS_NOALLOC_MAX_N, otherwise
+ * BCS_EINVAL with a message.  bc_out receives n FP64 values.
+ *
+ * Memory: the kernels' state lives in one static device array of about
+ * 42 MB (64 CTAs x 16,384 vertices), which every GPU that loads this library
+ * holds until the process exits.  The first call on a device looks up that
+ * array's address (cudaGetSymbolAddress) and may load the library's device
+ * code; make that first call before any stream capture.  Every call shares
+ * the array and resets the parts that must start cleared, so calls that
+ * overlap on the GPU (two streams, two threads) race and must not be issued.
+ */
+int bcs_bc_plain_noalloc(const bcs_csr *csr, const bcs_opts *opts, double *bc_out);
+
 /* The pieces bcs_shatter returns (library-owned, host memory). */
 typedef struct bcs_components bcs_components;
 

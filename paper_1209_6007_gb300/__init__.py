@@ -20,10 +20,10 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from ._lib import (BCS_EINVAL, BCS_ENODEV, BCS_ENOMEM, BCS_EOVERFLOW, BCS_ECUDA, BCS_ETIMEOUT, STEP_A, STEP_D,
+from ._lib import (NOALLOC_MAX_N, BCS_EINVAL, BCS_ENODEV, BCS_ENOMEM, BCS_EOVERFLOW, BCS_ECUDA, BCS_ETIMEOUT, STEP_A, STEP_D,
                    STEP_I, STEPS_ALL, ComponentsView, Csr, Opts, Stats, load)
 
-__all__ = ["bc_plain", "bc_shattered", "bc_sources", "debug_sssp", "shatter", "last_stats", "BcsError", "load",
+__all__ = ["bc_plain", "bc_plain_noalloc", "NOALLOC_MAX_N", "bc_shattered", "bc_sources", "debug_sssp", "shatter", "last_stats", "BcsError", "load",
            "STEP_D", "STEP_A", "STEP_I", "STEPS_ALL", "version"]
 
 _NAMES = {BCS_EINVAL: "EINVAL", BCS_ENOMEM: "ENOMEM", BCS_ECUDA: "ECUDA", BCS_ETIMEOUT: "ETIMEOUT",
@@ -112,6 +112,25 @@ def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool 
     a = _Args(rp, cl, steps=steps, delta_fp32=delta_fp32, stream=stream)
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_shattered(ctypes.byref(a.csr), ctypes.byref(a.opts), ptr))
+    return out
+
+
+def bc_plain_noalloc(row_ptr, col=None, *, delta_fp32: bool = False, stream=None):
+    """Plain Brandes without any device allocation by the library.
+
+    For callers that cannot let a library allocate GPU memory (all device
+    memory handed to their own pool, or a loop that must not enter the
+    allocator).  Needs CUDA torch tensors and at most NOALLOC_MAX_N vertices;
+    the result tensor is allocated here, by torch, not by the library.  The
+    library's state lives in a static device array shared by all calls, so
+    calls must not overlap on the GPU.
+    """
+    rp, cl = _csr_of(row_ptr, col)
+    a = _Args(rp, cl, delta_fp32=delta_fp32, stream=stream)
+    if not a.torch:
+        raise TypeError("bc_plain_noalloc needs CUDA tensors (device-resident graph and output)")
+    out, ptr = a.out(a.n)
+    _check(load().bcs_bc_plain_noalloc(ctypes.byref(a.csr), ctypes.byref(a.opts), ptr))
     return out
 
 

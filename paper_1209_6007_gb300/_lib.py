@@ -16,6 +16,7 @@ BCS_ENODEV = -6
 
 STEP_D, STEP_A, STEP_I = 1, 2, 4
 STEPS_ALL = 7
+NOALLOC_MAX_N = 16384
 
 c_i64, c_i32, c_u32, c_dbl, c_vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double, ctypes.c_void_p
 
@@ -50,6 +51,7 @@ SIGNATURES = {
     "bcs_bc_plain": (ctypes.c_int, [c_vp, c_vp, c_vp]),
     "bcs_bc_shattered": (ctypes.c_int, [c_vp, c_vp, c_vp]),
     "bcs_bc_sources": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp]),
+    "bcs_bc_plain_noalloc": (ctypes.c_int, [c_vp, c_vp, c_vp]),
     "bcs_debug_sssp": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "bcs_shatter": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "bcs_components_get": (ctypes.c_int, [c_vp, ctypes.POINTER(ComponentsView)]),

@@ -606,4 +606,82 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   return BCS_OK;
 }
 
+// ------------------------------------------- fixed-scratch plain Brandes
+// Plain Brandes (reach = ident = 1) over one component of n vertices on the
+// global-memory path, with every piece of device state carved out of a
+// caller-given scratch region instead of allocated.  Used by the
+// allocation-free entry point.
+
+__global__ void k_fixed_setup(LargeSrc *work, int32_t n, CompDesc *comp, CompDesc desc,
+                              unsigned long long *counter, int *err) {
+  for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) work[i] = LargeSrc{0, i};
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    *comp = desc;
+    *counter = 0ull;
+    *err = 0;
+  }
+}
+
+static size_t up256(size_t x) { return (x + 255) & ~(size_t)255; }
+static_assert(sizeof(LargeSrc) == FIXED_WORK_ITEM_BYTES, "work item size");
+static_assert(sizeof(CompDesc) <= 256, "component descriptor size");
+
+int launch_plain_fixed_scratch(Ctx &ctx, const int64_t *row, const int32_t *col, int32_t n, double *bc,
+                               unsigned char *scratch, int64_t nmax, int ctas, bool fp32) {
+  const size_t G = (size_t)ctas, N = (size_t)nmax;
+  unsigned char *p = scratch;
+  LargeSrc *work = (LargeSrc *)p;
+  p += up256(N * sizeof(LargeSrc));
+  CompDesc *comp = (CompDesc *)p;
+  p += up256(sizeof(CompDesc));
+  unsigned long long *counter = (unsigned long long *)p;
+  p += 256;
+  int *err = (int *)p;
+  p += 256;
+  LargeScratch sc;
+  sc.nmax = (int64_t)N;
+  sc.d = (int32_t *)p;
+  p += up256(G * N * 4);
+  sc.queue = (int32_t *)p;
+  p += up256(G * N * 4);
+  sc.sig = (double *)p;
+  p += up256(G * N * 8);
+  sc.coef = (double *)p;
+  p += up256(G * N * 8);
+  sc.acc = (double *)p;
+  p += up256(G * N * 8);
+  sc.lvl_start = (int32_t *)p;
+  p += up256(G * (N + 2) * 4);
+  sc.lvl_exp = (int32_t *)p;
+  // the region keeps whatever the previous call left: put back the states
+  // the kernel expects at its start (d = -1, sigma = 0, accumulators 0)
+  BCS_CUDA(cudaMemsetAsync(sc.d, 0xFF, G * N * 4, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(sc.sig, 0, G * N * 8, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(sc.acc, 0, G * N * 8, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(bc, 0, (size_t)n * sizeof(double), ctx.stream));
+  // n bounds the degree, hence the growth of path counts per level
+  CompDesc desc{0, 0, n, n, 0, (double)(n > 1 ? n : 1)};
+  k_fixed_setup<<<(n + 255) / 256, 256, 0, ctx.stream>>>(work, n, comp, desc, counter, err);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  Debug none{nullptr, nullptr, nullptr, nullptr};
+  BcInput in;
+  in.row = row;
+  in.col = col;
+  in.bcp = bc;
+  const int grid = (int)std::min<int64_t>(ctas, n);
+  if (fp32)
+    BCS_TRY((launch_large_t<false, false, true>(ctx, grid, work, n, counter, comp, in, sc, err, none, 0)));
+  else
+    BCS_TRY((launch_large_t<false, false, false>(ctx, grid, work, n, counter, comp, in, sc, err, none, 0)));
+  int h_err = 0;
+  BCS_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  if (h_err & ERR_OVERFLOW) {
+    set_error("shortest-path counts overflowed the FP64 range within one BFS level");
+    return BCS_EOVERFLOW;
+  }
+  return BCS_OK;
+}
+
 }  // namespace bcs
