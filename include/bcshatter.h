@@ -88,8 +88,12 @@ typedef struct bcs_stats {
   int64_t n_small_items;   /* shared-memory work items */
   int64_t n_large_sources; /* sources run on the global-memory path */
   int64_t kernel_launches; /* kernels this call launched */
+  int64_t bfs_levels;      /* levels of the BFS forest of the biconnected split */
+  int64_t dag_edges;       /* shortest-path DAG edges visited by Bc-Reach
+                              (summed over sources), when counted */
   double work_nm;          /* sum over pieces of n_c * m_c (m_c undirected) */
   double work_sources_entries; /* sum over processed sources of the piece's CSR entries */
+  double work_sources_vertices; /* sum over processed sources of the piece's vertices */
   double ms_total;         /* wall time of the call, host clock */
   double ms_upload;        /* host -> device copies of the input */
   double ms_validate;      /* CSR check */

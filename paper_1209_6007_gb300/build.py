@@ -18,7 +18,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libbcshatter.so")
 HEADERS = [os.path.join(ROOT, "include", "bcshatter.h")] + [
-    os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
+    os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".h", ".cuh"))]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",
                      "-Xcompiler", "-O2", "-I", os.path.join(ROOT, "include")]

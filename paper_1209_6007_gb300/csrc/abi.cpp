@@ -226,7 +226,7 @@ static int plain_impl(Ctx &ctx, const bcs_csr *h, const int64_t *src, int64_t k,
 // ------------------------------------------------------------ shattered
 struct Shattered {
   DBuf<int64_t> bcpre;
-  HostPieces hp;
+  DevPieces pc;
   DevMerged merged;
   std::vector<CompDesc> comps;
 };
@@ -261,59 +261,36 @@ static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t st
     ctx.stats.ms_peel = tm.stop_ms();
   }
   {
-    // pieces on the host
     StageTimer tm(ctx.stream);
     tm.start();
-    std::vector<uint8_t> h_alive(n);
-    std::vector<int32_t> h_reach(n), h_label(n);
-    std::vector<int64_t> h_N(n);
-    std::vector<int64_t> h_rp;
-    std::vector<int32_t> h_col;
-    BCS_CUDA(cudaMemcpyAsync(h_alive.data(), alive.p, n, cudaMemcpyDeviceToHost, ctx.stream));
-    BCS_CUDA(cudaMemcpyAsync(h_reach.data(), reach.p, n * 4, cudaMemcpyDeviceToHost, ctx.stream));
-    BCS_CUDA(cudaMemcpyAsync(h_label.data(), label.p, n * 4, cudaMemcpyDeviceToHost, ctx.stream));
-    BCS_CUDA(cudaMemcpyAsync(h_N.data(), N.p, n * 8, cudaMemcpyDeviceToHost, ctx.stream));
-    const int64_t *rp = h->row_ptr;
-    const int32_t *col = h->col;
-    if (h->on_device) {
-      h_rp.resize(n + 1);
-      h_col.resize(h->nnz);
-      BCS_CUDA(cudaMemcpyAsync(h_rp.data(), h->row_ptr, (n + 1) * 8, cudaMemcpyDeviceToHost, ctx.stream));
-      if (h->nnz) BCS_CUDA(cudaMemcpyAsync(h_col.data(), h->col, h->nnz * 4, cudaMemcpyDeviceToHost, ctx.stream));
-      rp = h_rp.data();
-      col = h_col.data();
-    }
-    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
-    BCS_TRY(host_build_pieces(n, rp, col, h_alive.data(), h_reach.data(), h_N.data(), h_label.data(), A, &S->hp));
+    BCS_TRY(device_pieces(ctx, in.g, alive.p, reach.p, N.p, label.p, A, &S->pc));
     ctx.stats.ms_blocks = tm.stop_ms();
   }
   {
     StageTimer tm(ctx.stream);
     tm.start();
-    BCS_TRY(device_merge(ctx, S->hp, I, &S->merged));
+    BCS_TRY(device_merge(ctx, S->pc, I, &S->merged));
     ctx.stats.ms_ident = tm.stop_ms();
   }
   // component descriptors
-  const HostPieces &hp = S->hp;
   const DevMerged &m = S->merged;
-  const int64_t P = hp.npieces();
+  const int64_t P = m.npieces;
   S->comps.resize(P);
   double work_nm = 0.0;
   for (int64_t p = 0; p < P; p++) {
-    int64_t mx = 1;
-    for (int64_t x = hp.piece_off[p]; x < hp.piece_off[p + 1]; x++) mx = std::max(mx, hp.srow[x + 1] - hp.srow[x]);
     CompDesc c;
     c.vtx_off = m.h_piece_off[p];
     c.row_off = m.h_piece_off[p];
     c.n = (int32_t)(m.h_piece_off[p + 1] - m.h_piece_off[p]);
-    c.maxdeg = (int32_t)mx;
+    c.maxdeg = std::max<int32_t>(1, m.h_piece_maxdeg[p]);
     c.nnz = m.h_piece_ent[p];
-    c.fan = (double)mx;
+    // sum of ident over a merged vertex's neighbours <= its degree before merging
+    c.fan = (double)c.maxdeg;
     S->comps[p] = c;
     work_nm += (double)c.n * (double)(c.nnz / 2);
   }
   ctx.stats.n_pieces = P;
-  ctx.stats.n_slots = hp.nslots();
+  ctx.stats.n_slots = m.nslots;
   ctx.stats.n_merged = m.nmerged;
   ctx.stats.n_entries = m.nentries;
   ctx.stats.work_nm = work_nm;
@@ -549,7 +526,9 @@ __attribute__((visibility("default"))) int bcs_shatter(const bcs_csr *csr, const
     const DevMerged &m = S.merged;
     const int64_t M = m.nmerged, E = m.nentries, SL = m.nslots, n = csr->n;
     c->piece_vtx_off = m.h_piece_off;
-    c->piece_N = S.hp.piece_N;
+    c->piece_N.resize(m.npieces);
+    if (m.npieces)
+      BCS_CUDA(cudaMemcpyAsync(c->piece_N.data(), m.piece_N.p, m.npieces * 8, cudaMemcpyDeviceToHost, ctx.stream));
     c->row_ptr.resize(M + 1);
     c->col.resize(E);
     c->org.resize(M);
@@ -557,7 +536,7 @@ __attribute__((visibility("default"))) int bcs_shatter(const bcs_csr *csr, const
     c->ident.resize(M);
     c->bc_corr.resize(M);
     c->bc_pre.resize(n);
-    std::vector<int32_t> s2m(SL);
+    std::vector<int32_t> s2m(SL), sorg(SL);
     BCS_CUDA(cudaMemcpyAsync(c->row_ptr.data(), m.mrow.p, (M + 1) * 8, cudaMemcpyDeviceToHost, ctx.stream));
     if (E) BCS_CUDA(cudaMemcpyAsync(c->col.data(), m.mcol.p, E * 4, cudaMemcpyDeviceToHost, ctx.stream));
     if (M) {
@@ -566,17 +545,21 @@ __attribute__((visibility("default"))) int bcs_shatter(const bcs_csr *csr, const
       BCS_CUDA(cudaMemcpyAsync(c->ident.data(), m.mident.p, M * 4, cudaMemcpyDeviceToHost, ctx.stream));
       BCS_CUDA(cudaMemcpyAsync(c->bc_corr.data(), m.mcorr.p, M * 8, cudaMemcpyDeviceToHost, ctx.stream));
     }
-    if (SL) BCS_CUDA(cudaMemcpyAsync(s2m.data(), m.slot_to_m.p, SL * 4, cudaMemcpyDeviceToHost, ctx.stream));
+    if (SL) {
+      BCS_CUDA(cudaMemcpyAsync(s2m.data(), m.slot_to_m.p, SL * 4, cudaMemcpyDeviceToHost, ctx.stream));
+      BCS_CUDA(cudaMemcpyAsync(sorg.data(), m.slot_org.p, SL * 4, cudaMemcpyDeviceToHost, ctx.stream));
+    }
     BCS_CUDA(cudaMemcpyAsync(c->bc_pre.data(), S.bcpre.p, n * 8, cudaMemcpyDeviceToHost, ctx.stream));
     BCS_CUDA(cudaStreamSynchronize(ctx.stream));
-    // members: pre-merge slots grouped by merged vertex (slots are ascending
-    // by original id inside a piece, so each member list comes out sorted)
+    // members: pre-merge slots grouped by merged vertex, each list ascending
     c->member_off.assign(M + 1, 0);
     for (int64_t x = 0; x < SL; x++) c->member_off[s2m[x] + 1]++;
     for (int64_t i = 0; i < M; i++) c->member_off[i + 1] += c->member_off[i];
     c->member.resize(SL);
     std::vector<int64_t> pos(c->member_off.begin(), c->member_off.end() - 1);
-    for (int64_t x = 0; x < SL; x++) c->member[pos[s2m[x]]++] = S.hp.slot_org[x];
+    for (int64_t x = 0; x < SL; x++) c->member[pos[s2m[x]]++] = sorg[x];
+    for (int64_t i = 0; i < M; i++)
+      std::sort(c->member.begin() + c->member_off[i], c->member.begin() + c->member_off[i + 1]);
     return BCS_OK;
   });
   if (rc != BCS_OK) {

@@ -75,10 +75,42 @@ __device__ __forceinline__ double group_max(const Group &g, double x, volatile d
 
 __device__ __forceinline__ int vld(const int32_t *p) { return *(volatile const int32_t *)p; }
 
-// binary exponent and [1,2) mantissa of a positive normal double
+// Binary exponent of a positive double and its [1,2) mantissa as FP32,
+// straight from the bit pattern (no FP64 instruction).  Only the rare
+// subnormal input takes the library route.
 __device__ __forceinline__ void split_pow2(double x, int &e, float &m) {
-  e = ilogb(x);
-  m = (float)scalbn(x, -e);
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex != 0) {
+    e = ex - 1023;
+    m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));
+  } else {
+    e = ilogb(x);
+    m = (float)scalbn(x, -e);
+  }
+}
+
+// 1/x for a positive double: Newton-Raphson iteration r <- r + r(1 - m r)
+// on the mantissa m in [1,2), seeded by the FP32 hardware reciprocal
+// approximation (relative error ~2^-23, so two steps reach FP64 precision),
+// then the exponent is put back by integer arithmetic on the bit pattern.
+// Inputs here are path counts scaled into [2^-900, 2^960], far from the
+// subnormal and overflow ends; anything else takes the IEEE division.
+__device__ __forceinline__ double recip_pos(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex < 64 || ex > 2000) return 1.0 / x;
+  const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff))));
+  const int fb = __float_as_int(rf);  // rf in (0.5, 1]: widen to FP64 through the bits
+  double r = __longlong_as_double(((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                  ((long long)(fb & 0x7fffff) << 29));
+  double e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)(ex - 1023) << 52));
 }
 
 template <bool FP32>
@@ -97,7 +129,7 @@ template <bool FP32>
 struct SrcState {
   int32_t *d;
   double *sig;
-  typename CoefT<FP32>::type *coef;
+  typename CoefT<FP32>::type *coef;  // phase 1 keeps sigma * ident here
   int32_t *queue;
   int32_t *lvl_start;  // levels + 2
   int32_t *lvl_exp;    // levels + 1
@@ -120,23 +152,24 @@ struct Debug {
 // One source of Bc-Reach over a component held as (row, col) with local ids.
 // RESET_BY_QUEUE: the state arrays start as d = -1, sigma = 0 and are put
 // back that way through the queue at the end (global-memory path); else they
-// are initialised here (shared-memory path).
-template <bool REACH, bool IDENT, bool FP32, bool ATOMIC_ACC, bool RESET_BY_QUEUE, typename RowT, typename ColT>
+// are initialised here (shared-memory path).  acc is private to the group
+// (plain adds).  dag counts the shortest-path DAG edges seen in phase 2.
+template <bool REACH, bool IDENT, bool FP32, bool RESET_BY_QUEUE, typename RowT, typename ColT>
 __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n, const RowT *__restrict__ row,
                                const ColT *__restrict__ col, const Weights wt, const SrcState<FP32> st,
-                               double *acc, const double fan, int *err, const Debug *dbg) {
+                               double *acc, const double fan, int *err, const Debug *dbg,
+                               unsigned long long &dag) {
   int32_t *const d = st.d;
   double *const sig = st.sig;
+  double *const sk = (double *)st.coef;  // sigma[v] * (v == s ? 1 : ident[v]) during phase 1
   if (!RESET_BY_QUEUE) {
-    for (int v = g.rank; v < n; v += g.size) {
-      d[v] = -1;
-      sig[v] = 0.0;
-    }
+    for (int v = g.rank; v < n; v += g.size) d[v] = -1;
     g.sync();
   }
   if (g.rank == 0) {
     d[s] = 0;
     sig[s] = 1.0;
+    sk[s] = 1.0;
     st.queue[0] = s;
     *st.qtail = 1;
     st.lvl_start[0] = 0;
@@ -148,33 +181,34 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   int lo = 0, hi = 1, L = 0, ecur = 0;
   double bound = 1.0;
   for (;;) {
+    // discover level L+1 (integer work only)
     for (int i = lo + g.rank; i < hi; i += g.size) {
       const int32_t v = st.queue[i];
-      double sv = sig[v];
-      if (IDENT && v != s) sv *= (double)wt.ident[v];
       const RowT eb = row[v], ee = row[v + 1];
       for (RowT e = eb; e < ee; e++) {
         const int32_t w = (int32_t)col[e];
-        int dw = vld(d + w);
-        if (dw < 0) {
-          const int old = atomicCAS(d + w, -1, L + 1);
-          if (old < 0) {
-            const int pos = atomicAdd(st.qtail, 1);
-            st.queue[pos] = w;
-            dw = L + 1;
-          } else {
-            dw = old;
-          }
-        }
-        if (dw == L + 1) atomicAdd(sig + w, sv);
+        if (vld(d + w) < 0 && atomicCAS(d + w, -1, L + 1) == -1) st.queue[atomicAdd(st.qtail, 1)] = w;
       }
     }
     g.sync();
     const int nhi = vld(st.qtail);
     g.sync();
     if (nhi == hi) break;
+    // path counts of level L+1, pulled from level L (one add per DAG edge)
+    for (int i = hi + g.rank; i < nhi; i += g.size) {
+      const int32_t w = st.queue[i];
+      double a = 0.0;
+      const RowT eb = row[w], ee = row[w + 1];
+      for (RowT e = eb; e < ee; e++) {
+        const int32_t u = (int32_t)col[e];
+        if (d[u] == L) a += IDENT ? sk[u] : sig[u];
+      }
+      sig[w] = a;
+      if (IDENT) sk[w] = a * (double)wt.ident[w];
+    }
     bound *= fan;
     if (bound > 0x1p900) {
+      g.sync();
       double m = 0.0;
       for (int i = hi + g.rank; i < nhi; i += g.size) m = fmax(m, sig[st.queue[i]]);
       m = group_max(g, m, st.red);
@@ -185,6 +219,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
         for (int i = hi + g.rank; i < nhi; i += g.size) {
           const int32_t w = st.queue[i];
           sig[w] = scalbn(sig[w], -k);
+          if (IDENT) sk[w] = scalbn(sk[w], -k);
         }
         m = scalbn(m, -k);
         ecur += k;
@@ -204,6 +239,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   g.sync();
   // ---------------------------------------------------------- phase 2
   const double Ws = (REACH ? (double)wt.reach[s] : 1.0) * (IDENT ? (double)wt.ident[s] : 1.0);
+  unsigned long long ndag = 0;
   for (int l = Lmax; l >= 0; l--) {
     const int a = st.lvl_start[l], b = st.lvl_start[l + 1];
     const int de = (l < Lmax) ? st.lvl_exp[l] - st.lvl_exp[l + 1] : 0;
@@ -211,8 +247,6 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
     for (int i = a + g.rank; i < b; i += g.size) {
       const int32_t v = st.queue[i];
       const double sv = sig[v];
-      const double init = REACH ? (double)(wt.reach[v] - 1) : 0.0;
-      const double kv = IDENT ? (double)wt.ident[v] : 1.0;
       double dv;
       if (!FP32) {
         double sum = 0.0;
@@ -220,11 +254,19 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
           const RowT eb = row[v], ee = row[v + 1];
           for (RowT e = eb; e < ee; e++) {
             const int32_t w = (int32_t)col[e];
-            if (d[w] == l + 1) sum += ((const double *)st.coef)[w];
+            if (d[w] == l + 1) {
+              sum += ((const double *)st.coef)[w];
+              ndag++;
+            }
           }
+          if (de != 0) sum *= scl;
         }
-        dv = init + sv * sum * scl;
-        ((double *)st.coef)[v] = kv * (1.0 + dv) / sv;
+        const double init = REACH ? (double)(wt.reach[v] - 1) : 0.0;
+        dv = fma(sv, sum, init);
+        if (l > 0) {  // the source's coefficient is never read
+          const double kv = IDENT ? (double)wt.ident[v] : 1.0;
+          ((double *)st.coef)[v] = fma(kv, dv, kv) * recip_pos(sv);
+        }
       } else {
         int ev;
         float mv;
@@ -239,24 +281,26 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
               const Coef32 cw = ((const Coef32 *)st.coef)[w];
               const int x = ev - cw.e;  // <= 0: sigma[v] <= sigma[w]
               if (x >= -126) sum = fmaf(cw.c, __int_as_float((127 + x) << 23), sum);
+              ndag++;
             }
           }
         }
-        const float df = (float)init + mv * sum;
+        const float df = fmaf(mv, sum, REACH ? (float)(wt.reach[v] - 1) : 0.0f);
         dv = (double)df;
-        Coef32 cv;
-        cv.c = (float)kv * (1.0f + df) / mv;
-        cv.e = ev;
-        ((Coef32 *)st.coef)[v] = cv;
+        if (l > 0) {
+          const float kv = IDENT ? (float)wt.ident[v] : 1.0f;
+          Coef32 cv;
+          cv.c = fmaf(kv, df, kv) / mv;
+          cv.e = ev;
+          ((Coef32 *)st.coef)[v] = cv;
+        }
       }
-      if (v != s && dv != 0.0) {
-        if (ATOMIC_ACC) atomicAdd(acc + v, Ws * dv);
-        else acc[v] += Ws * dv;
-      }
+      if (v != s && dv != 0.0) acc[v] = fma(Ws, dv, acc[v]);
       if (dbg) dbg->delta[v] = dv;
     }
     g.sync();
   }
+  dag += ndag;
   if (dbg) {
     for (int i = g.rank; i < hi; i += g.size) {
       const int32_t v = st.queue[i];
@@ -279,14 +323,18 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
 // ---------------------------------------------------------- small path
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// bytes of shared memory a component needs with `ng` concurrent sources
+__host__ __device__ inline size_t small_group_bytes(int64_t n) {
+  return align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 3;
+}
+
+// bytes of shared memory a component needs with `ng` concurrent sources:
+// the component (rows, columns, reach, ident) once, and per group the
+// distances, queue, path counts, coefficients and its own bc accumulator
 __host__ __device__ inline size_t small_smem_bytes(int64_t n, int64_t nnz, int ng, bool reach, bool ident) {
   size_t b = align16((size_t)(n + 1) * 4) + align16((size_t)nnz * 4);
   if (reach) b += align16((size_t)n * 4);
   if (ident) b += align16((size_t)n * 4);
-  b += align16((size_t)n * 8);  // accumulator
-  size_t per = align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 2;
-  return b + per * (size_t)ng;
+  return b + small_group_bytes(n) * (size_t)ng;
 }
 
 template <bool REACH, bool IDENT, bool FP32>
@@ -294,12 +342,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     const SmallItem *__restrict__ items, int nitems, int *item_counter, const CompDesc *__restrict__ comps,
     const int64_t *__restrict__ g_row, const int32_t *__restrict__ g_col, const int32_t *__restrict__ g_reach,
     const int32_t *__restrict__ g_ident, const int64_t *__restrict__ srcs, double *bcp, int32_t *lvl_scratch,
-    int lvl_stride, int *err) {
+    int lvl_stride, int *err, unsigned long long *dag_total) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ int s_qtail[SMALL_MAX_GROUPS];
   __shared__ double s_red[SMALL_MAX_GROUPS][16];
   const int tid = threadIdx.x;
+  unsigned long long dag = 0;
   for (;;) {
     if (tid == 0) s_item = atomicAdd(item_counter, 1);
     __syncthreads();
@@ -310,6 +359,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     const CompDesc c = comps[item.comp];
     const int n = c.n;
     const int nnz = (int)c.nnz;
+    const int ng = item.ngroups;
     unsigned char *p = smem;
     int32_t *row = (int32_t *)p;
     p += align16((size_t)(n + 1) * 4);
@@ -324,22 +374,24 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
       ident = (int32_t *)p;
       p += align16((size_t)n * 4);
     }
-    double *acc = (double *)p;
-    p += align16((size_t)n * 8);
+    const size_t per = small_group_bytes(n);
     const int64_t r0 = g_row[c.row_off];
     for (int v = tid; v <= n; v += SMALL_THREADS) row[v] = (int32_t)(g_row[c.row_off + v] - r0);
     for (int e = tid; e < nnz; e += SMALL_THREADS) col[e] = g_col[r0 + e];
     for (int v = tid; v < n; v += SMALL_THREADS) {
       if (REACH) reach[v] = g_reach[c.vtx_off + v];
       if (IDENT) ident[v] = g_ident[c.vtx_off + v];
-      acc[v] = 0.0;
+    }
+    // zero every group's accumulator
+    for (int x = tid; x < ng * n; x += SMALL_THREADS) {
+      const int gi = x / n, v = x - gi * n;
+      double *a = (double *)(p + per * gi + align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 2);
+      a[v] = 0.0;
     }
     __syncthreads();
-    const int ng = item.ngroups;
     const int gsize = SMALL_THREADS / ng;
     const int gid = tid / gsize;
     Group g{tid % gsize, gsize, 1 + gid};
-    const size_t per = align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 2;
     unsigned char *q = p + per * gid;
     SrcState<FP32> st;
     st.d = (int32_t *)q;
@@ -349,6 +401,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.sig = (double *)q;
     q += align16((size_t)n * 8);
     st.coef = (typename CoefT<FP32>::type *)q;
+    q += align16((size_t)n * 8);
+    double *acc = (double *)q;
     int32_t *lv = lvl_scratch + ((size_t)blockIdx.x * SMALL_MAX_GROUPS + gid) * (size_t)lvl_stride * 2;
     st.lvl_start = lv;
     st.lvl_exp = lv + lvl_stride;
@@ -357,13 +411,19 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     Weights wt{reach, ident};
     for (int i = item.s_begin + gid; i < item.s_end; i += ng) {
       const int32_t s = srcs ? (int32_t)srcs[i] : i;
-      bcreach_source<REACH, IDENT, FP32, true, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr);
+      bcreach_source<REACH, IDENT, FP32, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr, dag);
     }
     __syncthreads();
-    for (int v = tid; v < n; v += SMALL_THREADS)
-      if (acc[v] != 0.0) atomicAdd(bcp + c.vtx_off + v, acc[v]);
+    // add the groups' accumulators in group order and flush once
+    for (int v = tid; v < n; v += SMALL_THREADS) {
+      double t = 0.0;
+      for (int gi = 0; gi < ng; gi++)
+        t += ((const double *)(p + per * gi + align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 2))[v];
+      if (t != 0.0) atomicAdd(bcp + c.vtx_off + v, t);
+    }
     __syncthreads();
   }
+  if (dag_total && dag) atomicAdd(dag_total, dag);
 }
 
 // ---------------------------------------------------------- large path
@@ -389,7 +449,8 @@ template <bool REACH, bool IDENT, bool FP32>
 __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
     const LargeSrc *__restrict__ work, int64_t nwork, unsigned long long *counter, const CompDesc *__restrict__ comps,
     const int64_t *__restrict__ g_row, const int32_t *__restrict__ g_col, const int32_t *__restrict__ g_reach,
-    const int32_t *__restrict__ g_ident, double *bcp, LargeScratch sc, int *err, Debug dbg_in, int use_dbg) {
+    const int32_t *__restrict__ g_ident, double *bcp, LargeScratch sc, int *err, Debug dbg_in, int use_dbg,
+    unsigned long long *dag_total) {
   __shared__ unsigned long long s_idx;
   __shared__ int s_qtail;
   __shared__ double s_red[16];
@@ -405,6 +466,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
   st.qtail = &s_qtail;
   st.red = s_red;
   Group g{(int)threadIdx.x, (int)blockDim.x, 0};
+  unsigned long long dag = 0;
   int cur = -1;
   for (;;) {
     if (threadIdx.x == 0) s_idx = atomicAdd(counter, 1ull);
@@ -424,9 +486,10 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
     if (next < 0) break;
     const CompDesc c = comps[cur];
     Weights wt{REACH ? g_reach + c.vtx_off : nullptr, IDENT ? g_ident + c.vtx_off : nullptr};
-    bcreach_source<REACH, IDENT, FP32, false, true>(g, work[idx].s, c.n, g_row + c.row_off, g_col, wt, st, acc, c.fan,
-                                                    err, use_dbg ? &dbg_in : nullptr);
+    bcreach_source<REACH, IDENT, FP32, true>(g, work[idx].s, c.n, g_row + c.row_off, g_col, wt, st, acc, c.fan, err,
+                                             use_dbg ? &dbg_in : nullptr, dag);
   }
+  if (dag_total && dag) atomicAdd(dag_total, dag);
 }
 
 // bytes of global scratch per large-path CTA
@@ -436,11 +499,11 @@ static size_t large_scratch_bytes(int64_t nmax) { return (size_t)nmax * (4 + 4 +
 template <bool R, bool I, bool F>
 static int launch_small_t(Ctx &ctx, int grid, size_t smem, const SmallItem *items, int nitems, int *counter,
                           const CompDesc *comps, const BcInput &in, const int64_t *srcs, int32_t *lvl, int lvl_stride,
-                          int *err) {
+                          int *err, unsigned long long *dag) {
   auto kern = k_bcreach_small<R, I, F>;
   BCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<grid, SMALL_THREADS, smem, ctx.stream>>>(items, nitems, counter, comps, in.row, in.col, in.reach, in.ident,
-                                                 srcs, in.bcp, lvl, lvl_stride, err);
+                                                 srcs, in.bcp, lvl, lvl_stride, err, dag);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;
@@ -449,9 +512,10 @@ static int launch_small_t(Ctx &ctx, int grid, size_t smem, const SmallItem *item
 template <bool R, bool I, bool F>
 static int launch_large_t(Ctx &ctx, int grid, const LargeSrc *work, int64_t nwork, unsigned long long *counter,
                           const CompDesc *comps, const BcInput &in, const LargeScratch &sc, int *err,
-                          const Debug &dbg, int use_dbg) {
+                          const Debug &dbg, int use_dbg, unsigned long long *dag) {
   k_bcreach_large<R, I, F><<<grid, LARGE_THREADS, 0, ctx.stream>>>(work, nwork, counter, comps, in.row, in.col,
-                                                                  in.reach, in.ident, in.bcp, sc, err, dbg, use_dbg);
+                                                                  in.reach, in.ident, in.bcp, sc, err, dbg, use_dbg,
+                                                                  dag);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;
@@ -505,12 +569,13 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   }
   const int small_ctas = ctx.num_sms * 2;
   const double target = total_small_cost / (double)(small_ctas * 8) + 1.0;
-  double work_se = 0.0;
+  double work_se = 0.0, work_sv = 0.0;
   for (int64_t ci = 0; ci < C; ci++) {
     const CompDesc &c = comps[ci];
     if (c.n < 2) continue;
     const int64_t ns = po.sources ? po.nsources : c.n;
     work_se += (double)ns * (double)c.nnz;
+    work_sv += (double)ns * (double)c.n;
     if (ng_of[ci]) {
       const int ng = ng_of[ci];
       const double per = (double)(c.nnz + c.n);
@@ -530,12 +595,16 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   ctx.stats.n_small_items = (int64_t)items.size();
   ctx.stats.n_large_sources = (int64_t)work.size();
   ctx.stats.work_sources_entries = work_se;
+  ctx.stats.work_sources_vertices = work_sv;
   if (items.empty() && work.empty()) return BCS_OK;
 
   DBuf<CompDesc> d_comps;
   DBuf<int> d_err;
+  DBuf<unsigned long long> d_dag;
   BCS_TRY(d_comps.alloc(C, ctx.stream));
   BCS_TRY(d_err.alloc(4, ctx.stream));
+  BCS_TRY(d_dag.alloc(1, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(d_dag.p, 0, sizeof(unsigned long long), ctx.stream));
   BCS_CUDA(cudaMemcpyAsync(d_comps.p, comps.data(), C * sizeof(CompDesc), cudaMemcpyHostToDevice, ctx.stream));
   BCS_CUDA(cudaMemsetAsync(d_err.p, 0, 4 * sizeof(int), ctx.stream));
   DBuf<int64_t> d_srcs;
@@ -556,7 +625,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     BCS_TRY(lvl.alloc((size_t)grid * SMALL_MAX_GROUPS * lvl_stride * 2, ctx.stream));
     BCS_CUDA(cudaMemsetAsync(d_err.p + 1, 0, sizeof(int), ctx.stream));
     BCS_TRY(BCS_DISPATCH3(launch_small_t, R, I, F, ctx, grid, SMALL_SMEM, d_items.p, (int)items.size(), d_err.p + 1,
-                          d_comps.p, in, po.sources ? d_srcs.p : nullptr, lvl.p, lvl_stride, d_err.p));
+                          d_comps.p, in, po.sources ? d_srcs.p : nullptr, lvl.p, lvl_stride, d_err.p, d_dag.p));
     ctx.stats.ms_bcreach_small += tm.stop_ms();
   }
   if (!work.empty()) {
@@ -593,12 +662,15 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     LargeScratch sc{sd.p, sq.p, ssig.p, scoef.p, sacc.p, sls.p, sle.p, (int64_t)NM};
     Debug dbgs{po.dbg_d, po.dbg_sig, po.dbg_exp, po.dbg_delta};
     BCS_TRY(BCS_DISPATCH3(launch_large_t, R, I, F, ctx, (int)grid, d_work.p, (int64_t)work.size(), counter.p,
-                          d_comps.p, in, sc, d_err.p, dbgs, dbg ? 1 : 0));
+                          d_comps.p, in, sc, d_err.p, dbgs, dbg ? 1 : 0, d_dag.p));
     ctx.stats.ms_bcreach_large += tm.stop_ms();
   }
   int h_err = 0;
+  unsigned long long h_dag = 0;
   BCS_CUDA(cudaMemcpyAsync(&h_err, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaMemcpyAsync(&h_dag, d_dag.p, sizeof(h_dag), cudaMemcpyDeviceToHost, ctx.stream));
   BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  ctx.stats.dag_edges += (int64_t)h_dag;
   if (h_err & ERR_OVERFLOW) {
     set_error("shortest-path counts overflowed the FP64 range within one BFS level");
     return BCS_EOVERFLOW;
@@ -671,9 +743,9 @@ int launch_plain_fixed_scratch(Ctx &ctx, const int64_t *row, const int32_t *col,
   in.bcp = bc;
   const int grid = (int)std::min<int64_t>(ctas, n);
   if (fp32)
-    BCS_TRY((launch_large_t<false, false, true>(ctx, grid, work, n, counter, comp, in, sc, err, none, 0)));
+    BCS_TRY((launch_large_t<false, false, true>(ctx, grid, work, n, counter, comp, in, sc, err, none, 0, nullptr)));
   else
-    BCS_TRY((launch_large_t<false, false, false>(ctx, grid, work, n, counter, comp, in, sc, err, none, 0)));
+    BCS_TRY((launch_large_t<false, false, false>(ctx, grid, work, n, counter, comp, in, sc, err, none, 0, nullptr)));
   int h_err = 0;
   BCS_CUDA(cudaMemcpyAsync(&h_err, err, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
   BCS_CUDA(cudaStreamSynchronize(ctx.stream));

@@ -1,0 +1,567 @@
+// blocks_device.cu - the pieces of the graph left by degree-1 removal, built
+// on the device: biconnected components with the reach of every copy
+// (Sections 3.2.1-3.2.2, all articulation vertices at once as in Section 3.4),
+// or connected components when articulation shattering is off.
+//
+// Biconnected components follow Tarjan and Vishkin's characterisation over
+// any rooted spanning tree, here a BFS forest (one tree per component, rooted
+// at its smallest live vertex; every vertex takes its smallest-id neighbour of
+// the previous level as parent, so the forest is deterministic):
+//   pre[v]  preorder number, nd[v] subtree size,
+//   low[v]/high[v]  min/max of pre over v's subtree and the far ends of the
+//                   non-tree edges leaving it.
+// Tree edges e(w) = (parent[w], w) are joined (union-find) when
+//   (1) a non-tree edge {u, w} exists (in a BFS tree u and w are never
+//       ancestor and descendant, so every non-tree edge qualifies), or
+//   (2) w's subtree reaches outside its parent v's subtree:
+//       low[w] < pre[v] or high[w] >= pre[v] + nd[v]   (v not a root).
+// Each class of tree edges is one block; a non-tree edge belongs to the block
+// of its endpoints' tree edges.
+//
+// Copies and reach.  Every block has exactly one vertex that enters it from
+// outside, its top t (the parent of its topmost tree edges); every other
+// vertex of the block is there through its own tree edge (its home block).
+// With subR[x] the reach summed over x's subtree:
+//   top copy of block b:   reach = N_C - sum of subR[c] over b's tree edges
+//                           hanging directly below t
+//   home copy of v:        reach = reach[v] + sum of subR[c] over v's children
+//                           c that start other blocks
+// i.e. everything on the far side of the copy (Eq. 4); each block's reach
+// sums to N_C.
+//
+// Slots (piece, vertex) are numbered per block: the top copy first, then the
+// home copies in ascending vertex id (stable radix sort by block).  Each
+// copy's row is the matching subsequence of the input row, so rows stay in
+// ascending original id.
+#include <algorithm>
+
+#include "common.h"
+#include "uf.cuh"
+
+namespace bcs {
+
+static inline int gridv(int64_t work, int block, int max_blocks) {
+  int64_t b = (work + block - 1) / block;
+  if (b < 1) b = 1;
+  if (b > max_blocks) b = max_blocks;
+  return (int)b;
+}
+
+#define GRID_STRIDE(i, n) \
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += (int64_t)gridDim.x * blockDim.x)
+
+__device__ __forceinline__ void push_aggr(int32_t *queue, unsigned long long *count, int32_t v) {
+  unsigned mask = __activemask();
+  int leader = __ffs(mask) - 1;
+  int lane = threadIdx.x & 31;
+  int rank = __popc(mask & ((1u << lane) - 1));
+  unsigned long long base = 0;
+  if (lane == leader) base = atomicAdd(count, (unsigned long long)__popc(mask));
+  base = __shfl_sync(mask, base, leader);
+  queue[base + rank] = v;
+}
+
+__global__ void k_iota_i32_dev(int64_t n, int32_t *p) {
+  GRID_STRIDE(i, n) { p[i] = (int32_t)i; }
+}
+
+// live degree of every live vertex (0 for removed ones)
+__global__ void k_alive_deg(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const uint8_t *__restrict__ alive, int32_t *adeg) {
+  GRID_STRIDE(v, n) {
+    int32_t d = 0;
+    if (alive[v])
+      for (int64_t k = rp[v]; k < rp[v + 1]; k++) d += alive[col[k]];
+    adeg[v] = d;
+  }
+}
+
+__global__ void k_roots(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ label,
+                        int32_t *root_of) {
+  GRID_STRIDE(v, n) {
+    if (adeg[v] > 0) atomicMin(root_of + label[v], (int32_t)v);
+  }
+}
+
+__global__ void k_bfs_init(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ label,
+                           const int32_t *__restrict__ root_of, int32_t *level, int32_t *parent, int32_t *order,
+                           unsigned long long *tail) {
+  GRID_STRIDE(v, n) {
+    parent[v] = -1;
+    const bool root = adeg[v] > 0 && root_of[label[v]] == (int32_t)v;
+    level[v] = root ? 0 : -1;
+    if (root) push_aggr(order, tail, (int32_t)v);
+  }
+}
+
+__global__ void k_bfs_expand(int64_t lo, int64_t hi, const int32_t *__restrict__ order_in, const int64_t *__restrict__ rp,
+                             const int32_t *__restrict__ col, const uint8_t *__restrict__ alive, int32_t *level,
+                             int32_t L, int32_t *order_out, unsigned long long *tail) {
+  GRID_STRIDE(i, hi - lo) {
+    const int32_t v = order_in[lo + i];
+    for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+      const int32_t w = col[k];
+      if (!alive[w] || uf_vload(level + w) >= 0) continue;
+      if (atomicCAS(level + w, -1, L + 1) == -1) push_aggr(order_out, tail, w);
+    }
+  }
+}
+
+// parent = smallest-id neighbour on the previous level
+__global__ void k_bfs_parent(int64_t lo, int64_t hi, const int32_t *__restrict__ order, const int64_t *__restrict__ rp,
+                             const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
+                             const int32_t *__restrict__ level, int32_t L, int32_t *parent) {
+  GRID_STRIDE(i, hi - lo) {
+    const int32_t w = order[lo + i];
+    int32_t p = INT32_MAX;
+    for (int64_t k = rp[w]; k < rp[w + 1]; k++) {
+      const int32_t v = col[k];
+      if (alive[v] && level[v] == L && v < p) p = v;
+    }
+    parent[w] = p;
+  }
+}
+
+__global__ void k_tree_init(int64_t cnt, const int32_t *__restrict__ order, const int32_t *__restrict__ reach,
+                            int32_t *nd, int64_t *subR, int32_t *pre) {
+  GRID_STRIDE(i, cnt) {
+    const int32_t v = order[i];
+    nd[v] = 1;
+    subR[v] = reach[v];
+    pre[v] = 0;
+  }
+}
+
+__global__ void k_up_sizes(int64_t lo, int64_t hi, const int32_t *__restrict__ order, const int32_t *__restrict__ parent,
+                           int32_t *nd, int64_t *subR) {
+  GRID_STRIDE(i, hi - lo) {
+    const int32_t v = order[lo + i];
+    const int32_t p = parent[v];
+    atomicAdd(nd + p, nd[v]);
+    atomicAdd((unsigned long long *)(subR + p), (unsigned long long)subR[v]);
+  }
+}
+
+// preorder of v's children, in row order: pre[c] = pre[v] + 1 + sizes of earlier children
+__global__ void k_preorder(int64_t lo, int64_t hi, const int32_t *__restrict__ order, const int64_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
+                           const int32_t *__restrict__ parent, const int32_t *__restrict__ nd, int32_t *pre) {
+  GRID_STRIDE(i, hi - lo) {
+    const int32_t v = order[lo + i];
+    int32_t acc = pre[v] + 1;
+    for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+      const int32_t w = col[k];
+      if (alive[w] && parent[w] == v) {
+        pre[w] = acc;
+        acc += nd[w];
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ bool is_tree_edge(const int32_t *parent, int32_t u, int32_t w) {
+  return parent[w] == u || parent[u] == w;
+}
+
+__global__ void k_lowhigh_local(int64_t cnt, const int32_t *__restrict__ order, const int64_t *__restrict__ rp,
+                                const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
+                                const int32_t *__restrict__ parent, const int32_t *__restrict__ pre, int32_t *low,
+                                int32_t *high) {
+  GRID_STRIDE(i, cnt) {
+    const int32_t u = order[i];
+    int32_t lo = pre[u], hi = pre[u];
+    for (int64_t k = rp[u]; k < rp[u + 1]; k++) {
+      const int32_t w = col[k];
+      if (!alive[w] || is_tree_edge(parent, u, w)) continue;
+      lo = min(lo, pre[w]);
+      hi = max(hi, pre[w]);
+    }
+    low[u] = lo;
+    high[u] = hi;
+  }
+}
+
+__global__ void k_up_lowhigh(int64_t lo, int64_t hi, const int32_t *__restrict__ order, const int32_t *__restrict__ parent,
+                             int32_t *low, int32_t *high) {
+  GRID_STRIDE(i, hi - lo) {
+    const int32_t v = order[lo + i];
+    const int32_t p = parent[v];
+    atomicMin(low + p, low[v]);
+    atomicMax(high + p, high[v]);
+  }
+}
+
+// union-find over tree edges, identified by their child vertex
+__global__ void k_tv_unite(int64_t cnt, const int32_t *__restrict__ order, const int64_t *__restrict__ rp,
+                           const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
+                           const int32_t *__restrict__ parent, const int32_t *__restrict__ level,
+                           const int32_t *__restrict__ pre, const int32_t *__restrict__ nd,
+                           const int32_t *__restrict__ low, const int32_t *__restrict__ high, int32_t *uf) {
+  GRID_STRIDE(i, cnt) {
+    const int32_t u = order[i];
+    if (level[u] == 0) continue;  // roots carry no tree edge
+    for (int64_t k = rp[u]; k < rp[u + 1]; k++) {
+      const int32_t w = col[k];
+      if (w > u && alive[w] && !is_tree_edge(parent, u, w)) uf_unite(uf, u, w);  // rule (1)
+    }
+    const int32_t v = parent[u];
+    if (level[v] > 0 && (low[u] < pre[v] || high[u] >= pre[v] + nd[v])) uf_unite(uf, u, v);  // rule (2)
+  }
+}
+
+// flag[v] = 1 for the representative tree edge of each block
+__global__ void k_tv_finish(int64_t cnt, const int32_t *__restrict__ order, const int32_t *__restrict__ level, int32_t *uf,
+                            int32_t *blk, int64_t *flag) {
+  GRID_STRIDE(i, cnt) {
+    const int32_t v = order[i];
+    if (level[v] == 0) continue;
+    const int32_t r = uf_find(uf, v);
+    blk[v] = r;
+    flag[v] = (r == v);
+  }
+}
+
+// block index of each non-root tree vertex; tops, side sums and block sizes
+__global__ void k_blocks_top(int64_t cnt, const int32_t *__restrict__ order, const int32_t *__restrict__ level,
+                             const int32_t *__restrict__ parent, const int32_t *__restrict__ blk,
+                             const int64_t *__restrict__ bidx, const int64_t *__restrict__ subR, int32_t *bid, int32_t *top,
+                             int64_t *side, int64_t *childblk, int64_t *bcnt) {
+  GRID_STRIDE(i, cnt) {
+    const int32_t c = order[i];
+    if (level[c] == 0) continue;
+    const int32_t b = (int32_t)bidx[blk[c]];
+    bid[c] = b;
+    atomicAdd((unsigned long long *)(bcnt + b), 1ull);
+    const int32_t p = parent[c];
+    const int32_t bp = level[p] > 0 ? (int32_t)bidx[blk[p]] : -1;
+    if (bp != b) {
+      top[b] = p;
+      atomicAdd((unsigned long long *)(side + b), (unsigned long long)subR[c]);
+      if (bp >= 0) atomicAdd((unsigned long long *)(childblk + p), (unsigned long long)subR[c]);
+    }
+  }
+}
+
+// connected-component pieces: every live vertex with a live edge has one slot
+__global__ void k_cc_pieces(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ label,
+                            const int64_t *__restrict__ pidx, int32_t *bid, int64_t *bcnt) {
+  GRID_STRIDE(v, n) {
+    if (adeg[v] == 0) continue;
+    const int32_t b = (int32_t)pidx[label[v]];
+    bid[v] = b;
+    atomicAdd((unsigned long long *)(bcnt + b), 1ull);
+  }
+}
+
+__global__ void k_flag_label_used(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ label,
+                                  int64_t *flag) {
+  GRID_STRIDE(v, n) {
+    if (adeg[v] > 0) flag[label[v]] = 1;
+  }
+}
+
+// list (key = piece, value = vertex) of the vertices holding a home slot, in
+// ascending vertex order
+__global__ void k_home_list(int64_t n, const int64_t *__restrict__ hpos, const int64_t *__restrict__ hflag,
+                            const int32_t *__restrict__ bid, uint32_t *keys, int32_t *vals) {
+  GRID_STRIDE(v, n) {
+    if (!hflag[v]) continue;
+    keys[hpos[v]] = (uint32_t)bid[v];
+    vals[hpos[v]] = (int32_t)v;
+  }
+}
+
+__global__ void k_home_flags(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ level, bool art,
+                             int64_t *hflag) {
+  GRID_STRIDE(v, n) { hflag[v] = art ? (adeg[v] > 0 && level[v] > 0) : (adeg[v] > 0); }
+}
+
+__global__ void k_home_slots(int64_t nh, const uint32_t *__restrict__ keys, const int32_t *__restrict__ vals, int tops,
+                             const int32_t *__restrict__ reach, const int64_t *__restrict__ childblk, int32_t *home_slot,
+                             int32_t *slot_org, int32_t *slot_reach, int32_t *slot_piece) {
+  GRID_STRIDE(i, nh) {
+    const int32_t v = vals[i];
+    const int32_t b = (int32_t)keys[i];
+    const int64_t s = i + (tops ? (int64_t)b + 1 : 0);
+    home_slot[v] = (int32_t)s;
+    slot_org[s] = v;
+    slot_reach[s] = reach[v] + (int32_t)(childblk ? childblk[v] : 0);
+    slot_piece[s] = b;
+  }
+}
+
+__global__ void k_top_slots(int64_t nb, const int64_t *__restrict__ boff, const int32_t *__restrict__ top,
+                            const int64_t *__restrict__ side, const int64_t *__restrict__ N, int32_t *top_slot,
+                            int32_t *slot_org, int32_t *slot_reach, int32_t *slot_piece, int64_t *piece_N) {
+  GRID_STRIDE(b, nb) {
+    const int64_t s = boff[b];
+    const int32_t t = top[b];
+    top_slot[b] = (int32_t)s;
+    slot_org[s] = t;
+    slot_reach[s] = (int32_t)(N[t] - side[b]);
+    slot_piece[s] = (int32_t)b;
+    piece_N[b] = N[t];
+  }
+}
+
+__global__ void k_piece_N_cc(int64_t nh, const int32_t *__restrict__ vals, const uint32_t *__restrict__ keys,
+                             const int64_t *__restrict__ N, int64_t *piece_N) {
+  GRID_STRIDE(i, nh) { piece_N[keys[i]] = N[vals[i]]; }
+}
+
+// block of the edge {v, w} and the slots of both ends in it
+__device__ __forceinline__ void edge_slots(bool art, int32_t v, int32_t w, const int32_t *parent, const int32_t *level,
+                                           const int32_t *bid, const int32_t *home_slot, const int32_t *top_slot,
+                                           int32_t &sv, int32_t &sw) {
+  if (!art) {
+    sv = home_slot[v];
+    sw = home_slot[w];
+    return;
+  }
+  const int32_t hv = level[v] > 0 ? bid[v] : -1;
+  const int32_t be = parent[w] == v ? bid[w] : hv;  // tree edge to a child, or v's own block
+  sv = be == hv ? home_slot[v] : top_slot[be];
+  sw = (level[w] > 0 && bid[w] == be) ? home_slot[w] : top_slot[be];
+}
+
+__global__ void k_slot_degrees(int64_t cnt, const int32_t *__restrict__ verts, bool art, const int64_t *__restrict__ rp,
+                               const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
+                               const int32_t *__restrict__ parent, const int32_t *__restrict__ level,
+                               const int32_t *__restrict__ bid, const int32_t *__restrict__ home_slot,
+                               const int32_t *__restrict__ top_slot, int64_t *sdeg) {
+  GRID_STRIDE(i, cnt) {
+    const int32_t v = verts[i];
+    for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+      const int32_t w = col[k];
+      if (!alive[w]) continue;
+      int32_t sv, sw;
+      edge_slots(art, v, w, parent, level, bid, home_slot, top_slot, sv, sw);
+      sdeg[sv]++;  // every slot of v is written only by v's thread
+    }
+  }
+}
+
+__global__ void k_slot_fill(int64_t cnt, const int32_t *__restrict__ verts, bool art, const int64_t *__restrict__ rp,
+                            const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
+                            const int32_t *__restrict__ parent, const int32_t *__restrict__ level,
+                            const int32_t *__restrict__ bid, const int32_t *__restrict__ home_slot,
+                            const int32_t *__restrict__ top_slot, int64_t *cursor, int32_t *scol) {
+  GRID_STRIDE(i, cnt) {
+    const int32_t v = verts[i];
+    for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+      const int32_t w = col[k];
+      if (!alive[w]) continue;
+      int32_t sv, sw;
+      edge_slots(art, v, w, parent, level, bid, home_slot, top_slot, sv, sw);
+      scol[cursor[sv]++] = sw;
+    }
+  }
+}
+
+__global__ void k_piece_maxdeg(int64_t nslots, const int64_t *__restrict__ srow, const int32_t *__restrict__ slot_piece,
+                               int32_t *maxdeg) {
+  GRID_STRIDE(s, nslots) { atomicMax(maxdeg + slot_piece[s], (int32_t)(srow[s + 1] - srow[s])); }
+}
+
+static int read_i64(Ctx &ctx, const int64_t *d, int64_t *h, int count) {
+  BCS_CUDA(cudaMemcpyAsync(h, d, count * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  return BCS_OK;
+}
+
+int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32_t *reach, const int64_t *N,
+                  const int32_t *label, bool art, DevPieces *out) {
+  const int64_t n = g.n;
+  const int B = 256;
+  const int gv = gridv(n, B, ctx.num_sms * 32);
+  DBuf<int32_t> adeg, level, parent, order, bid, home_slot, pre, nd, low, high, uf, blk, root_of, top, top_slot;
+  DBuf<int64_t> subR, side, childblk, flag, fscan, bcnt, boff, tot, hflag, hpos;
+  BCS_TRY(adeg.alloc(n, ctx.stream));
+  BCS_TRY(level.alloc(n, ctx.stream));
+  BCS_TRY(parent.alloc(n, ctx.stream));
+  BCS_TRY(bid.alloc(n, ctx.stream));
+  BCS_TRY(home_slot.alloc(n, ctx.stream));
+  BCS_TRY(flag.alloc(n, ctx.stream));
+  BCS_TRY(fscan.alloc(n, ctx.stream));
+  BCS_TRY(tot.alloc(2, ctx.stream));
+  BCS_TRY(hflag.alloc(n, ctx.stream));
+  BCS_TRY(hpos.alloc(n, ctx.stream));
+  k_alive_deg<<<gv, B, 0, ctx.stream>>>(n, g.rp, g.col, alive, adeg.p);
+  ctx.launches++;
+
+  int64_t nb = 0;           // pieces
+  int64_t tree_cnt = 0;     // vertices in the forest (art) / with a slot
+  std::vector<int64_t> lvl_off;
+  if (art) {
+    BCS_TRY(root_of.alloc(n, ctx.stream));
+    BCS_TRY(order.alloc(n, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(root_of.p, 0x7f, n * sizeof(int32_t), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(tot.p, 0, 2 * sizeof(int64_t), ctx.stream));
+    k_roots<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, root_of.p);
+    k_bfs_init<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, root_of.p, level.p, parent.p, order.p,
+                                         (unsigned long long *)tot.p);
+    ctx.launches += 2;
+    BCS_CUDA(cudaGetLastError());
+    int64_t cntv = 0;
+    BCS_TRY(read_i64(ctx, tot.p, &cntv, 1));
+    lvl_off.push_back(0);
+    lvl_off.push_back(cntv);
+    // level-synchronous BFS; the host reads each level's size
+    for (int32_t L = 0;; L++) {
+      const int64_t lo = lvl_off[L], hi = lvl_off[L + 1];
+      if (hi == lo) break;
+      k_bfs_expand<<<gridv(hi - lo, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(
+          lo, hi, order.p, g.rp, g.col, alive, level.p, L, order.p, (unsigned long long *)tot.p);
+      ctx.launches++;
+      BCS_CUDA(cudaGetLastError());
+      int64_t nhi = 0;
+      BCS_TRY(read_i64(ctx, tot.p, &nhi, 1));
+      if (nhi > hi) {
+        k_bfs_parent<<<gridv(nhi - hi, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(hi, nhi, order.p, g.rp, g.col, alive,
+                                                                                 level.p, L, parent.p);
+        ctx.launches++;
+      }
+      lvl_off.push_back(nhi);
+      if (nhi == hi) break;
+    }
+    lvl_off.pop_back();  // last entry repeats the previous one
+    const int nlev = (int)lvl_off.size() - 1;
+    tree_cnt = lvl_off.back();
+    // subtree sizes and reach sums, bottom-up
+    BCS_TRY(pre.alloc(n, ctx.stream));
+    BCS_TRY(nd.alloc(n, ctx.stream));
+    BCS_TRY(subR.alloc(n, ctx.stream));
+    BCS_TRY(low.alloc(n, ctx.stream));
+    BCS_TRY(high.alloc(n, ctx.stream));
+    BCS_TRY(uf.alloc(n, ctx.stream));
+    BCS_TRY(blk.alloc(n, ctx.stream));
+    const int gt = gridv(tree_cnt, B, ctx.num_sms * 32);
+    k_tree_init<<<gt, B, 0, ctx.stream>>>(tree_cnt, order.p, reach, nd.p, subR.p, pre.p);
+    ctx.launches++;
+    for (int L = nlev - 1; L >= 1; L--) {
+      const int64_t lo = lvl_off[L], hi = lvl_off[L + 1];
+      k_up_sizes<<<gridv(hi - lo, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(lo, hi, order.p, parent.p, nd.p, subR.p);
+      ctx.launches++;
+    }
+    for (int L = 0; L < nlev - 1; L++) {
+      const int64_t lo = lvl_off[L], hi = lvl_off[L + 1];
+      k_preorder<<<gridv(hi - lo, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(lo, hi, order.p, g.rp, g.col, alive,
+                                                                           parent.p, nd.p, pre.p);
+      ctx.launches++;
+    }
+    k_lowhigh_local<<<gt, B, 0, ctx.stream>>>(tree_cnt, order.p, g.rp, g.col, alive, parent.p, pre.p, low.p, high.p);
+    ctx.launches++;
+    for (int L = nlev - 1; L >= 1; L--) {
+      const int64_t lo = lvl_off[L], hi = lvl_off[L + 1];
+      k_up_lowhigh<<<gridv(hi - lo, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(lo, hi, order.p, parent.p, low.p, high.p);
+      ctx.launches++;
+    }
+    // union-find over tree edges
+    k_iota_i32_dev<<<gv, B, 0, ctx.stream>>>(n, uf.p);
+    BCS_CUDA(cudaMemsetAsync(flag.p, 0, n * sizeof(int64_t), ctx.stream));
+    k_tv_unite<<<gt, B, 0, ctx.stream>>>(tree_cnt, order.p, g.rp, g.col, alive, parent.p, level.p, pre.p, nd.p, low.p,
+                                        high.p, uf.p);
+    k_tv_finish<<<gt, B, 0, ctx.stream>>>(tree_cnt, order.p, level.p, uf.p, blk.p, flag.p);
+    ctx.launches += 3;
+    BCS_CUDA(cudaGetLastError());
+    BCS_TRY(launch_exclusive_scan(ctx, flag.p, fscan.p, n, tot.p));
+    BCS_TRY(read_i64(ctx, tot.p, &nb, 1));
+    BCS_TRY(top.alloc(nb, ctx.stream));
+    BCS_TRY(side.alloc(nb, ctx.stream));
+    BCS_TRY(bcnt.alloc(nb, ctx.stream));
+    BCS_TRY(childblk.alloc(n, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(side.p, 0, nb * sizeof(int64_t), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(childblk.p, 0, n * sizeof(int64_t), ctx.stream));
+    BCS_TRY(launch_fill_i64(ctx, bcnt.p, nb, 1));  // the top copy
+    k_blocks_top<<<gt, B, 0, ctx.stream>>>(tree_cnt, order.p, level.p, parent.p, blk.p, fscan.p, subR.p, bid.p, top.p,
+                                          side.p, childblk.p, bcnt.p);
+    ctx.launches++;
+    BCS_CUDA(cudaGetLastError());
+  } else {
+    // pieces = connected components (of the live graph) with a live edge
+    BCS_CUDA(cudaMemsetAsync(flag.p, 0, n * sizeof(int64_t), ctx.stream));
+    k_flag_label_used<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, flag.p);
+    ctx.launches++;
+    BCS_TRY(launch_exclusive_scan(ctx, flag.p, fscan.p, n, tot.p));
+    BCS_TRY(read_i64(ctx, tot.p, &nb, 1));
+    BCS_TRY(bcnt.alloc(nb, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(bcnt.p, 0, nb * sizeof(int64_t), ctx.stream));
+    k_cc_pieces<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, fscan.p, bid.p, bcnt.p);
+    ctx.launches++;
+    BCS_CUDA(cudaGetLastError());
+  }
+  // slots: offsets per piece, then the home copies sorted by (piece, vertex)
+  BCS_TRY(out->piece_off.alloc(nb + 1, ctx.stream));
+  BCS_TRY(launch_exclusive_scan(ctx, bcnt.p, out->piece_off.p, nb, tot.p));
+  BCS_CUDA(cudaMemcpyAsync(out->piece_off.p + nb, tot.p, sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx.stream));
+  k_home_flags<<<gv, B, 0, ctx.stream>>>(n, adeg.p, level.p, art, hflag.p);
+  ctx.launches++;
+  BCS_TRY(launch_exclusive_scan(ctx, hflag.p, hpos.p, n, tot.p + 1));
+  int64_t h2[2];
+  BCS_TRY(read_i64(ctx, tot.p, h2, 2));
+  const int64_t S = h2[0], H = h2[1];
+  out->npieces = nb;
+  out->nslots = S;
+  DBuf<uint32_t> keys, tkeys;
+  DBuf<int32_t> vals, tvals;
+  BCS_TRY(keys.alloc(H, ctx.stream));
+  BCS_TRY(vals.alloc(H, ctx.stream));
+  BCS_TRY(tkeys.alloc(H, ctx.stream));
+  BCS_TRY(tvals.alloc(H, ctx.stream));
+  k_home_list<<<gv, B, 0, ctx.stream>>>(n, hpos.p, hflag.p, bid.p, keys.p, vals.p);
+  ctx.launches++;
+  int bits = 1;
+  while (bits < 32 && ((int64_t)1 << bits) < nb) bits++;
+  BCS_TRY(radix_sort_pairs(ctx, keys.p, vals.p, tkeys.p, tvals.p, H, bits));
+  BCS_TRY(out->slot_org.alloc(S, ctx.stream));
+  BCS_TRY(out->slot_reach.alloc(S, ctx.stream));
+  BCS_TRY(out->slot_piece.alloc(S, ctx.stream));
+  BCS_TRY(out->piece_N.alloc(nb, ctx.stream));
+  k_home_slots<<<gridv(H, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(H, keys.p, vals.p, art ? 1 : 0, reach,
+                                                                    art ? childblk.p : nullptr, home_slot.p,
+                                                                    out->slot_org.p, out->slot_reach.p,
+                                                                    out->slot_piece.p);
+  ctx.launches++;
+  if (art) {
+    BCS_TRY(top_slot.alloc(nb, ctx.stream));
+    k_top_slots<<<gridv(nb, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(nb, out->piece_off.p, top.p, side.p, N,
+                                                                      top_slot.p, out->slot_org.p, out->slot_reach.p,
+                                                                      out->slot_piece.p, out->piece_N.p);
+  } else {
+    k_piece_N_cc<<<gridv(H, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(H, vals.p, keys.p, N, out->piece_N.p);
+  }
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  // rows: each vertex's thread walks its input row once per pass
+  const int32_t *verts = art ? order.p : vals.p;
+  const int64_t nverts = art ? tree_cnt : H;
+  const int gw = gridv(nverts, B, ctx.num_sms * 32);
+  DBuf<int64_t> sdeg, cursor;
+  BCS_TRY(sdeg.alloc(S + 1, ctx.stream));
+  BCS_TRY(cursor.alloc(S + 1, ctx.stream));
+  BCS_TRY(out->srow.alloc(S + 1, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(sdeg.p, 0, (S + 1) * sizeof(int64_t), ctx.stream));
+  k_slot_degrees<<<gw, B, 0, ctx.stream>>>(nverts, verts, art, g.rp, g.col, alive, parent.p, level.p, bid.p,
+                                           home_slot.p, art ? top_slot.p : nullptr, sdeg.p);
+  ctx.launches++;
+  BCS_TRY(launch_exclusive_scan(ctx, sdeg.p, out->srow.p, S + 1, tot.p));
+  BCS_CUDA(cudaMemcpyAsync(cursor.p, out->srow.p, (S + 1) * sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx.stream));
+  int64_t E = 0;
+  BCS_TRY(read_i64(ctx, tot.p, &E, 1));
+  out->nentries = E;
+  BCS_TRY(out->scol.alloc(E, ctx.stream));
+  k_slot_fill<<<gw, B, 0, ctx.stream>>>(nverts, verts, art, g.rp, g.col, alive, parent.p, level.p, bid.p, home_slot.p,
+                                        art ? top_slot.p : nullptr, cursor.p, out->scol.p);
+  ctx.launches++;
+  BCS_TRY(out->piece_maxdeg.alloc(nb, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(out->piece_maxdeg.p, 0, nb * sizeof(int32_t), ctx.stream));
+  k_piece_maxdeg<<<gridv(S, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(S, out->srow.p, out->slot_piece.p,
+                                                                      out->piece_maxdeg.p);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  ctx.stats.bfs_levels = art ? (int64_t)lvl_off.size() - 1 : 0;
+  ctx.stats.n_slots = S;
+  return BCS_OK;
+}
+
+}  // namespace bcs

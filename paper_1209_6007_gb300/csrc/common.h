@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/bcshatter.h"
@@ -53,6 +54,11 @@ struct DBuf {
     p = nullptr;
     n = 0;
   }
+  void swap(DBuf &o) {
+    std::swap(p, o.p);
+    std::swap(n, o.n);
+    std::swap(s, o.s);
+  }
   int alloc(size_t count, cudaStream_t stream) {
     release();
     s = stream;
@@ -98,27 +104,30 @@ struct DevGraph {
   const int32_t *col = nullptr;
 };
 
-// Pieces (components of the shattered graph) before identical merging:
-// slots are (piece, original vertex) pairs, contiguous per piece, ascending
-// by original id inside a piece; scol holds global slot ids.
-struct HostPieces {
-  std::vector<int64_t> piece_off;  // npieces+1 (slot offsets)
-  std::vector<int64_t> piece_N;    // npieces
-  std::vector<int32_t> slot_org;   // nslots
-  std::vector<int32_t> slot_reach; // nslots
-  std::vector<int32_t> slot_piece; // nslots
-  std::vector<int64_t> srow;       // nslots+1
-  std::vector<int32_t> scol;       // entries (global slot ids)
-  int64_t npieces() const { return (int64_t)piece_off.size() - 1; }
-  int64_t nslots() const { return (int64_t)slot_org.size(); }
+// Pieces (components of the shattered graph) before identical merging, on
+// the device: slots are (piece, original vertex) pairs, contiguous per piece;
+// scol holds global slot ids; each row is in ascending original id.
+struct DevPieces {
+  int64_t npieces = 0, nslots = 0, nentries = 0;
+  DBuf<int64_t> piece_off;     // npieces+1 (slot offsets)
+  DBuf<int64_t> piece_N;       // npieces
+  DBuf<int64_t> srow;          // nslots+1
+  DBuf<int32_t> slot_org;      // nslots
+  DBuf<int32_t> slot_reach;    // nslots
+  DBuf<int32_t> slot_piece;    // nslots
+  DBuf<int32_t> scol;          // nentries
+  DBuf<int32_t> piece_maxdeg;  // npieces
 };
 
-// Build the pieces on the host from the graph left by degree-1 removal.
-// alive[v]: vertex still present; reach[v]: its reach; ccN[v]: size of its
-// connected component in the input; cclab[v]: component label.
-int host_build_pieces(int64_t n, const int64_t *rp, const int32_t *col, const uint8_t *alive,
-                      const int32_t *reach, const int64_t *ccN, const int32_t *cclab, bool articulation,
-                      HostPieces *out);
+// Build the pieces from the graph left by degree-1 removal: alive[v] vertex
+// still present, reach[v] its reach, N[v] size of its connected component in
+// the input, label[v] that component's id.  art: biconnected components
+// (else connected components).
+int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32_t *reach, const int64_t *N,
+                  const int32_t *label, bool art, DevPieces *out);
+
+// Stable LSD radix sort of (key, value) pairs; keys < 2^key_bits.
+int radix_sort_pairs(Ctx &ctx, uint32_t *keys, int32_t *vals, uint32_t *tk, int32_t *tv, int64_t n, int key_bits);
 
 // Pieces after identical merging, on the device.
 struct DevMerged {
@@ -135,10 +144,11 @@ struct DevMerged {
   DBuf<int32_t> slot_to_m;   // nslots -> merged vertex
   std::vector<int64_t> h_piece_off;  // host copies for planning
   std::vector<int64_t> h_piece_ent;  // entries per piece
+  std::vector<int32_t> h_piece_maxdeg;  // largest degree per piece before merging
   int32_t max_ident = 1;
 };
 
-int device_merge(Ctx &ctx, const HostPieces &hp, bool identical, DevMerged *out);
+int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out);
 
 // ------------------------------------------------------- graph kernels
 int launch_validate(Ctx &ctx, const DevGraph &g, int *d_flags);
@@ -149,6 +159,7 @@ int launch_bc_init(Ctx &ctx, int64_t n, const int64_t *d_bcpre, double *d_bc);
 int launch_mapback(Ctx &ctx, int64_t nslots, const int32_t *slot_org, const int32_t *slot_to_m,
                    const double *bcp, double *d_bc);
 int launch_fill_i32(Ctx &ctx, int32_t *p, int64_t n, int32_t v);
+int launch_fill_i64(Ctx &ctx, int64_t *p, int64_t n, int64_t v);
 int launch_exclusive_scan(Ctx &ctx, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total);
 
 // ------------------------------------------------------- Bc-Reach

@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "uf.cuh"
 
 namespace bcs {
 
@@ -89,36 +90,6 @@ int launch_validate(Ctx &ctx, const DevGraph &g, int *d_flags) {
 }
 
 // ---------------------------------------------------- connected components
-// Union-find with hooking of the larger root under the smaller one (so
-// every parent pointer decreases and the root is the smallest id) and path
-// halving in find.
-__device__ __forceinline__ int32_t vload(const int32_t *p) { return *(volatile const int32_t *)p; }
-
-__device__ int32_t uf_find(int32_t *p, int32_t x) {
-  for (;;) {
-    int32_t px = vload(p + x);
-    if (px == x) return x;
-    int32_t gpx = vload(p + px);
-    if (gpx == px) return px;
-    *(volatile int32_t *)(p + x) = gpx;
-    x = gpx;
-  }
-}
-
-__device__ void uf_unite(int32_t *p, int32_t a, int32_t b) {
-  for (;;) {
-    a = uf_find(p, a);
-    b = uf_find(p, b);
-    if (a == b) return;
-    if (a < b) {
-      int32_t t = a;
-      a = b;
-      b = t;
-    }
-    if (atomicCAS(p + a, a, b) == a) return;
-  }
-}
-
 __global__ void k_iota(int64_t n, int32_t *p) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
     p[v] = (int32_t)v;
@@ -324,6 +295,18 @@ __global__ void k_fill_i32(int32_t *p, int64_t n, int32_t v) {
 int launch_fill_i32(Ctx &ctx, int32_t *p, int64_t n, int32_t v) {
   if (n == 0) return BCS_OK;
   k_fill_i32<<<grid_for(n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(p, n, v);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+__global__ void k_fill_i64(int64_t *p, int64_t n, int64_t v) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) p[i] = v;
+}
+
+int launch_fill_i64(Ctx &ctx, int64_t *p, int64_t n, int64_t v) {
+  if (n == 0) return BCS_OK;
+  k_fill_i64<<<grid_for(n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(p, n, v);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;

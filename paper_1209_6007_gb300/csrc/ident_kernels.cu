@@ -12,8 +12,9 @@
 // on collision): every slot gets an order-free 64-bit hash of its open
 // neighbourhood (sum of a 64-bit mix of the neighbours' original ids) and of
 // its closed one; (piece, hash, degree, reach) goes into an open-addressing
-// table whose value is the smallest slot with that key; every slot then
-// compares its sorted row with the row of that candidate exactly.  A
+// table whose value is the member with the smallest original id; every slot
+// then compares its row (ascending original ids) with that candidate's row
+// exactly.  A
 // fingerprint collision can only make a merge fail, never a wrong merge.
 //
 // Terms added when a class of K members of reach r is merged into one
@@ -62,9 +63,11 @@ __global__ void k_ident_hash(int64_t nslots, const int64_t *__restrict__ srow, c
 }
 
 // Insert both fingerprints; slot_of[2x+t] = table index of slot x's key.
+// The table value keeps the smallest (original id, slot) of its key, so the
+// class representative is the member with the smallest original id.
 __global__ void k_ident_insert(int64_t nslots, const uint64_t *__restrict__ fp_open,
-                               const uint64_t *__restrict__ fp_closed, unsigned long long *keys, int32_t *vals,
-                               uint64_t mask, int64_t *slot_of) {
+                               const uint64_t *__restrict__ fp_closed, const int32_t *__restrict__ org,
+                               unsigned long long *keys, unsigned long long *vals, uint64_t mask, int64_t *slot_of) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nslots; x += (int64_t)gridDim.x * blockDim.x) {
     for (int t = 0; t < 2; t++) {
       const uint64_t f = t ? fp_closed[x] : fp_open[x];
@@ -72,7 +75,7 @@ __global__ void k_ident_insert(int64_t nslots, const uint64_t *__restrict__ fp_o
       for (uint64_t probe = 0; probe <= mask; probe++) {
         unsigned long long old = atomicCAS(keys + i, 0ull, (unsigned long long)f);
         if (old == 0ull || old == f) {
-          atomicMin(vals + i, (int32_t)x);
+          atomicMin(vals + i, ((unsigned long long)(uint32_t)org[x] << 32) | (unsigned long long)(uint32_t)x);
           slot_of[2 * x + t] = (int64_t)i;
           break;
         }
@@ -118,12 +121,12 @@ __device__ bool rows_equal_closed(const int64_t *srow, const int32_t *scol, int6
 
 __global__ void k_ident_verify(int64_t nslots, const int64_t *__restrict__ srow, const int32_t *__restrict__ scol,
                                const int32_t *__restrict__ reach, const int32_t *__restrict__ piece,
-                               const int32_t *__restrict__ vals, const int64_t *__restrict__ slot_of, int32_t *cls,
-                               int8_t *typ) {
+                               const unsigned long long *__restrict__ vals, const int64_t *__restrict__ slot_of,
+                               int32_t *cls, int8_t *typ) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nslots; x += (int64_t)gridDim.x * blockDim.x) {
     int32_t rep = (int32_t)x;
     for (int t = 0; t < 2 && rep == x; t++) {
-      const int32_t c = vals[slot_of[2 * x + t]];
+      const int32_t c = (int32_t)(vals[slot_of[2 * x + t]] & 0xffffffffull);
       if (c == x) continue;
       if (piece[c] != piece[x] || reach[c] != reach[x]) continue;
       bool ok = t ? rows_equal_closed(srow, scol, x, c) : rows_equal_open(srow, scol, x, c);
@@ -217,26 +220,14 @@ __global__ void k_iota32(int64_t n, int32_t *p) {
     p[i] = (int32_t)i;
 }
 
-template <class T>
-static int upload(Ctx &ctx, DBuf<T> &d, const std::vector<T> &h) {
-  BCS_TRY(d.alloc(h.size(), ctx.stream));
-  if (!h.empty()) BCS_CUDA(cudaMemcpyAsync(d.p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, ctx.stream));
-  return BCS_OK;
-}
-
-int device_merge(Ctx &ctx, const HostPieces &hp, bool identical, DevMerged *out) {
-  const int64_t P = hp.npieces(), S = hp.nslots(), E = (int64_t)hp.scol.size();
+int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
+  const int64_t P = pc.npieces, S = pc.nslots;
   out->npieces = P;
   out->nslots = S;
-  DBuf<int64_t> piece_off, srow;
-  DBuf<int32_t> scol, spiece, sreach;
-  BCS_TRY(upload(ctx, piece_off, hp.piece_off));
-  BCS_TRY(upload(ctx, out->piece_N, hp.piece_N));
-  BCS_TRY(upload(ctx, srow, hp.srow));
-  BCS_TRY(upload(ctx, scol, hp.scol));
-  BCS_TRY(upload(ctx, spiece, hp.slot_piece));
-  BCS_TRY(upload(ctx, sreach, hp.slot_reach));
-  BCS_TRY(upload(ctx, out->slot_org, hp.slot_org));
+  const int64_t *piece_off = pc.piece_off.p, *srow = pc.srow.p;
+  const int32_t *scol = pc.scol.p, *spiece = pc.slot_piece.p, *sreach = pc.slot_reach.p;
+  out->slot_org.swap(pc.slot_org);
+  out->piece_N.swap(pc.piece_N);
   const int block = 256;
   const int gs = grid_for(S, block, ctx.num_sms * 32);
 
@@ -246,8 +237,7 @@ int device_merge(Ctx &ctx, const HostPieces &hp, bool identical, DevMerged *out)
   BCS_TRY(cls.alloc(S, ctx.stream));
   if (identical && S > 0) {
     DBuf<uint64_t> fo, fc;
-    DBuf<unsigned long long> keys;
-    DBuf<int32_t> vals;
+    DBuf<unsigned long long> keys, vals;
     DBuf<int64_t> slot_of;
     uint64_t tsize = 1;
     while (tsize < (uint64_t)(4 * S)) tsize <<= 1;
@@ -260,16 +250,15 @@ int device_merge(Ctx &ctx, const HostPieces &hp, bool identical, DevMerged *out)
     BCS_TRY(typ.alloc(S, ctx.stream));
     BCS_TRY(corr.alloc(S, ctx.stream));
     BCS_CUDA(cudaMemsetAsync(keys.p, 0, tsize * sizeof(unsigned long long), ctx.stream));
-    BCS_CUDA(cudaMemsetAsync(vals.p, 0x7f, tsize * sizeof(int32_t), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(vals.p, 0xFF, tsize * sizeof(unsigned long long), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(cnt.p, 0, S * sizeof(int32_t), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(typ.p, 0, S * sizeof(int8_t), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(corr.p, 0, S * sizeof(double), ctx.stream));
-    k_ident_hash<<<gs, block, 0, ctx.stream>>>(S, srow.p, scol.p, out->slot_org.p, sreach.p, spiece.p, fo.p, fc.p);
-    k_ident_insert<<<gs, block, 0, ctx.stream>>>(S, fo.p, fc.p, keys.p, vals.p, tsize - 1, slot_of.p);
-    k_ident_verify<<<gs, block, 0, ctx.stream>>>(S, srow.p, scol.p, sreach.p, spiece.p, vals.p, slot_of.p, cls.p,
-                                                 typ.p);
+    k_ident_hash<<<gs, block, 0, ctx.stream>>>(S, srow, scol, out->slot_org.p, sreach, spiece, fo.p, fc.p);
+    k_ident_insert<<<gs, block, 0, ctx.stream>>>(S, fo.p, fc.p, out->slot_org.p, keys.p, vals.p, tsize - 1, slot_of.p);
+    k_ident_verify<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, spiece, vals.p, slot_of.p, cls.p, typ.p);
     k_ident_count<<<gs, block, 0, ctx.stream>>>(S, cls.p, cnt.p);
-    k_ident_corr<<<gs, block, 0, ctx.stream>>>(S, srow.p, scol.p, sreach.p, cls.p, cnt.p, typ.p, corr.p);
+    k_ident_corr<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, cls.p, cnt.p, typ.p, corr.p);
     ctx.launches += 5;
     BCS_CUDA(cudaGetLastError());
   } else if (S > 0) {
@@ -284,7 +273,7 @@ int device_merge(Ctx &ctx, const HostPieces &hp, bool identical, DevMerged *out)
   BCS_TRY(mrow_scan.alloc(S + 1, ctx.stream));
   BCS_TRY(totals.alloc(2, ctx.stream));
   if (S > 0) {
-    k_merge_degrees<<<gs, block, 0, ctx.stream>>>(S, srow.p, scol.p, cls.p, keep.p, ndeg.p);
+    k_merge_degrees<<<gs, block, 0, ctx.stream>>>(S, srow, scol, cls.p, keep.p, ndeg.p);
     ctx.launches++;
   }
   BCS_TRY(launch_exclusive_scan(ctx, keep.p, mslot.p, S, totals.p));
@@ -305,15 +294,15 @@ int device_merge(Ctx &ctx, const HostPieces &hp, bool identical, DevMerged *out)
   BCS_TRY(out->piece_off.alloc(P + 1, ctx.stream));
   BCS_CUDA(cudaMemcpyAsync(out->mrow.p + M, totals.p + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx.stream));
   if (S > 0) {
-    k_merge_emit<<<gs, block, 0, ctx.stream>>>(S, srow.p, scol.p, cls.p, spiece.p, piece_off.p, mslot.p, mrow_scan.p,
-                                               out->slot_org.p, sreach.p, identical ? cnt.p : nullptr,
+    k_merge_emit<<<gs, block, 0, ctx.stream>>>(S, srow, scol, cls.p, spiece, piece_off, mslot.p, mrow_scan.p,
+                                               out->slot_org.p, sreach, identical ? cnt.p : nullptr,
                                                identical ? corr.p : nullptr, out->mrow.p, out->mcol.p, out->morg.p,
                                                out->mreach.p, out->mident.p, out->mcorr.p, out->slot_to_m.p);
     ctx.launches++;
   }
   DBuf<int64_t> prow;
   BCS_TRY(prow.alloc(P + 1, ctx.stream));
-  k_piece_bounds<<<grid_for(P + 1, block, ctx.num_sms * 8), block, 0, ctx.stream>>>(P, piece_off.p, mslot.p, M,
+  k_piece_bounds<<<grid_for(P + 1, block, ctx.num_sms * 8), block, 0, ctx.stream>>>(P, piece_off, mslot.p, M,
                                                                                     out->mrow.p, out->piece_off.p,
                                                                                     prow.p);
   ctx.launches++;
@@ -323,6 +312,10 @@ int device_merge(Ctx &ctx, const HostPieces &hp, bool identical, DevMerged *out)
   BCS_CUDA(cudaMemcpyAsync(out->h_piece_off.data(), out->piece_off.p, (P + 1) * sizeof(int64_t),
                            cudaMemcpyDeviceToHost, ctx.stream));
   BCS_CUDA(cudaMemcpyAsync(hrow.data(), prow.p, (P + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
+  out->h_piece_maxdeg.resize(P);
+  if (P)
+    BCS_CUDA(cudaMemcpyAsync(out->h_piece_maxdeg.data(), pc.piece_maxdeg.p, P * sizeof(int32_t),
+                             cudaMemcpyDeviceToHost, ctx.stream));
   if (identical && S > 0) {
     // largest ident, for the path-count growth bound of the Bc-Reach kernels
     std::vector<int32_t> hc(S);

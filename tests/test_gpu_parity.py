@@ -159,6 +159,25 @@ def test_partition_bit_exact(gpu, steps):
         assert got == ref, g.name
 
 
+def holey_grid(side, frac, seed):
+    """side x side grid with a seeded fraction of its edges removed."""
+    g = gg.grid(side, side)
+    e = g.edges()
+    keep = np.random.default_rng(seed).random(e.shape[0]) >= frac
+    return gg.from_edges(g.n, e[keep], f"holey_grid({side},{frac})")
+
+
+@pytest.mark.parametrize("g", [holey_grid(40, 0.25, 1), holey_grid(30, 0.4, 2), gg.config(3, scale_pct=1),
+                               gg.config(4, scale_pct=1)], ids=lambda g: g.name)
+def test_partition_and_bc_structured(gpu, g):
+    """Biconnected split on high-diameter, holey and twin-heavy graphs."""
+    got = canon_gpu(gpu.shatter(g.row_ptr, g.col, steps=ALL))
+    assert got == canon_oracle(oracle.shatter(g, ALL))
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col), ref) <= TOL64
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, delta_fp32=True), ref) <= TOL32
+
+
 # --------------------------------------------- full size, sampled sources
 def test_articulation_full_size_sources_vs_oracle(gpu):
     """Config 2 at full size: plain Brandes on 256 seeded sources against the
