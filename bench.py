@@ -128,6 +128,20 @@ def workload(scale: int):
                "n": g.n, "m": g.m, "seed": g.meta["seed"], "delta": "fp64"}
 
 
+def measured_traffic():
+    """DRAM bytes per launch of the Bc-Reach kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "bcreach_small_articulation.json")))
+        src = open(os.path.join(ROOT, "paper_1209_6007_gb300", "csrc", "bcreach.cu"), "rb").read()
+        if rec.get("source_sha1") == hashlib.sha1(src).hexdigest():
+            return float(rec["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        pass
+    return None
+
+
 def cpu_baseline(g, seconds: float) -> dict:
     """The oracle (plain Brandes, FP64) on a bounded sample of sources."""
     import oracle
@@ -238,10 +252,14 @@ def run_ours(args):
     if not args.no_e2e:
         for _ in range(2):
             bcs.bc_shattered(g.row_ptr, g.col)
-        t0 = time.perf_counter()
+        te = 0.0
         for _ in range(args.steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
             bcs.bc_shattered(g.row_ptr, g.col)
-        te = max_over_ranks(time.perf_counter() - t0, world)
+            te += time.perf_counter() - t0
+        te = max_over_ranks(te, world)
         e2e = {"value": world * nm * args.steps / te / 1e9, "unit": "GTEPS",
                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes), "d2h_bytes_per_step": int(g.n * 8)}
 
@@ -274,17 +292,26 @@ def run_ours(args):
     err32 = float((b32 - ref).abs().max() / max(1.0, float(ref.abs().max())))
     fp32 = {"gteps": nm / t32 / 1e9, "rel_err_vs_fp64": err32}
 
-    # roofline of the dominant kernel class (Bc-Reach small-component path):
-    # algorithmic bytes = each piece's CSR read once per source plus the
-    # per-vertex state written and re-read once per source
-    ms_small = stages.get("ms_bcreach_small", 0.0) + stages.get("ms_bcreach_large", 0.0)
-    se = float(st["work_sources_entries"])
-    algo_bytes = se * 4.0 * 2 + float(st["n_merged"]) * 0.0
-    roof = {"bound": "hbm", "achieved": (algo_bytes / (ms_small / 1e3) / 1e9) if ms_small > 0 else None,
-            "peak": hbm_peak, "unit": "GB/s", "traffic": None, "kernel": "bcreach (small+large)",
-            "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)" if peaks else "fallback 6800 GB/s"}
-    if roof["achieved"]:
-        roof["frac"] = roof["achieved"] / hbm_peak
+    # roofline of the dominant kernel (Bc-Reach, shared-memory path): it is
+    # bound by GB300's FP64 pipe, so the figure is algorithmic FP64 FLOP/s:
+    # 2 per shortest-path DAG edge (path-count add, dependency add) and 9 per
+    # (source, vertex) (sigma*ident, the dependency FMA, the coefficient
+    # k(1+delta)/sigma counted as FMA + divide, and the bc FMA).  The peak is
+    # GB300's FP64 rate, 2 FP64 FMA per clock per SM (nominal 1.25 TFLOP/s),
+    # at the SM clock sampled during the timed region.
+    dag = float(st["dag_edges"])
+    vsrc = float(st["work_sources_vertices"])
+    ms_k = st["ms_bcreach_small"] + st["ms_bcreach_large"]
+    flop = 2.0 * dag + 9.0 * vsrc
+    sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp64_peak = n_sm * 4.0 * sm_mhz * 1e6 / 1e12  # TFLOP/s
+    achieved = flop / (ms_k / 1e3) / 1e12 if ms_k > 0 else None
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": (achieved / fp64_peak) if achieved else None, "traffic": measured_traffic(),
+            "kernel": "k_bcreach_small (FP64 dependencies)",
+            "peak_source": f"derived: {n_sm} SMs x 4 FP64 FLOP/clk x {sm_mhz:.0f} MHz (sampled)",
+            "work": {"dag_edges": dag, "source_vertices": vsrc, "flop": flop, "ms": ms_k}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
@@ -294,6 +321,7 @@ def run_ours(args):
                            "parallelism": f"{world} replica(s)"},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
                 "stages_ms": stages, "pieces": int(st["n_pieces"]), "merged_vertices": int(st["n_merged"]),
+                "bfs_levels": int(st["bfs_levels"]),
                 "work_nm_pieces": float(st["work_nm"]), "plain": plain,
                 "speedup_vs_plain": (value / plain["gteps"]) if plain else None, "fp32_delta": fp32,
                 "wall_s": wall}

@@ -75,7 +75,9 @@ typedef struct bcs_opts {
                          candidates once per shape and caching the choice */
   int32_t device;     /* CUDA device ordinal; -1 = the current device */
   void *stream;       /* cudaStream_t for all device work; NULL = default */
-  int64_t max_wait;   /* reserved (0) */
+  int64_t max_wait;   /* polls a device-side wait (grid barrier) makes before
+                         the call gives up with BCS_ETIMEOUT; 0 = default
+                         (about a second); < 0 = give up at once (tests) */
 } bcs_opts;
 
 /* Per-call statistics of the calling thread's last successful call. */
@@ -91,6 +93,8 @@ typedef struct bcs_stats {
   int64_t bfs_levels;      /* levels of the BFS forest of the biconnected split */
   int64_t dag_edges;       /* shortest-path DAG edges visited by Bc-Reach
                               (summed over sources), when counted */
+  int64_t n_ms_batches;    /* 32-source batches on the large-piece path */
+  int64_t batch_ctas;      /* CTAs of the 32-source launch */
   double work_nm;          /* sum over pieces of n_c * m_c (m_c undirected) */
   double work_sources_entries; /* sum over processed sources of the piece's CSR entries */
   double work_sources_vertices; /* sum over processed sources of the piece's vertices */
@@ -123,6 +127,19 @@ int bcs_bc_plain(const bcs_csr *csr, const bcs_opts *opts, double *bc_out);
  * equals Eq. 1 on the input graph (Theorem 1 and its corollaries).
  */
 int bcs_bc_shattered(const bcs_csr *csr, const bcs_opts *opts, double *bc_out);
+
+/*
+ * Betweenness of many independent graphs at once (the paper's Eq. 1 applied
+ * to each graph): `packed` holds count graphs in one CSR, graph g owning the
+ * vertex ids [graph_vtx_off[g], graph_vtx_off[g+1]) (host array of count+1
+ * ascending offsets, graph_vtx_off[0] = 0, graph_vtx_off[count] = n).  No
+ * edge may join two graphs (BCS_EINVAL otherwise).  Because no shortest path
+ * crosses graphs, the pieces of all graphs are shattered together and share
+ * one persistent Bc-Reach launch; bc_out[v] is v's betweenness within its
+ * own graph.
+ */
+int bcs_bc_shattered_batch(const int64_t *graph_vtx_off, int64_t count, const bcs_csr *packed,
+                           const bcs_opts *opts, double *bc_out);
 
 /*
  * Partial Brandes sum over a list of k sources (Eq. 2):

@@ -23,7 +23,7 @@ import numpy as np
 from ._lib import (NOALLOC_MAX_N, BCS_EINVAL, BCS_ENODEV, BCS_ENOMEM, BCS_EOVERFLOW, BCS_ECUDA, BCS_ETIMEOUT, STEP_A, STEP_D,
                    STEP_I, STEPS_ALL, ComponentsView, Csr, Opts, Stats, load)
 
-__all__ = ["bc_plain", "bc_plain_noalloc", "NOALLOC_MAX_N", "bc_shattered", "bc_sources", "debug_sssp", "shatter", "last_stats", "BcsError", "load",
+__all__ = ["bc_plain", "bc_plain_noalloc", "bc_shattered_batch", "NOALLOC_MAX_N", "bc_shattered", "bc_sources", "debug_sssp", "shatter", "last_stats", "BcsError", "load",
            "STEP_D", "STEP_A", "STEP_I", "STEPS_ALL", "version"]
 
 _NAMES = {BCS_EINVAL: "EINVAL", BCS_ENOMEM: "ENOMEM", BCS_ECUDA: "ECUDA", BCS_ETIMEOUT: "ETIMEOUT",
@@ -48,14 +48,14 @@ def _is_torch(x) -> bool:
 class _Args:
     """Keeps the marshalled buffers alive for the duration of one call."""
 
-    def __init__(self, row_ptr, col, steps=STEPS_ALL, delta_fp32=False, stream=None):
+    def __init__(self, row_ptr, col, steps=STEPS_ALL, delta_fp32=False, stream=None, max_wait=0):
         self.keep = []
         self.torch = _is_torch(row_ptr)
         self.opts = Opts()
         self.opts.steps = steps
         self.opts.delta_fp32 = 1 if delta_fp32 else 0
         self.opts.device = -1
-        self.opts.max_wait = 0
+        self.opts.max_wait = max_wait
         if self.torch:
             import torch
             if row_ptr.device.type != "cuda" or col.device.type != "cuda":
@@ -106,12 +106,29 @@ def bc_plain(row_ptr, col=None, *, delta_fp32: bool = False, stream=None):
     return out
 
 
-def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool = False, stream=None):
-    """Shattered + compressed BC (Section 3), equal to Eq. 1 on the input."""
+def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool = False, stream=None,
+                 max_wait: int = 0):
+    """Shattered + compressed BC (Section 3), equal to Eq. 1 on the input.
+
+    max_wait bounds the polls of device-side waits (0: default, < 0: give up
+    at once, which makes the call fail with ETIMEOUT; for tests)."""
     rp, cl = _csr_of(row_ptr, col)
-    a = _Args(rp, cl, steps=steps, delta_fp32=delta_fp32, stream=stream)
+    a = _Args(rp, cl, steps=steps, delta_fp32=delta_fp32, stream=stream, max_wait=max_wait)
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_shattered(ctypes.byref(a.csr), ctypes.byref(a.opts), ptr))
+    return out
+
+
+def bc_shattered_batch(vtx_off, row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool = False,
+                       stream=None):
+    """BC of many independent graphs packed in one CSR (graph g owns the
+    vertices [vtx_off[g], vtx_off[g+1]); no edge may join two graphs)."""
+    rp, cl = _csr_of(row_ptr, col)
+    a = _Args(rp, cl, steps=steps, delta_fp32=delta_fp32, stream=stream)
+    off = np.ascontiguousarray(np.asarray(vtx_off, dtype=np.int64).reshape(-1))
+    out, ptr = a.out(a.n)
+    _check(load().bcs_bc_shattered_batch(off.ctypes.data, off.size - 1, ctypes.byref(a.csr), ctypes.byref(a.opts),
+                                         ptr))
     return out
 
 

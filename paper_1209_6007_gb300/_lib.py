@@ -33,7 +33,7 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(name, c_i64) for name in (
         "n_pieces", "n_slots", "n_merged", "n_entries", "peel_rounds", "n_small_items",
-        "n_large_sources", "kernel_launches", "bfs_levels", "dag_edges")] + [(name, c_dbl) for name in (
+        "n_large_sources", "kernel_launches", "bfs_levels", "dag_edges", "n_ms_batches", "batch_ctas")] + [(name, c_dbl) for name in (
         "work_nm", "work_sources_entries", "work_sources_vertices", "ms_total", "ms_upload", "ms_validate", "ms_cc", "ms_peel",
         "ms_blocks", "ms_ident", "ms_plan", "ms_bcreach_small", "ms_bcreach_large", "ms_mapback",
         "ms_download")]
@@ -52,6 +52,7 @@ SIGNATURES = {
     "bcs_bc_shattered": (ctypes.c_int, [c_vp, c_vp, c_vp]),
     "bcs_bc_sources": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp]),
     "bcs_bc_plain_noalloc": (ctypes.c_int, [c_vp, c_vp, c_vp]),
+    "bcs_bc_shattered_batch": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_vp]),
     "bcs_debug_sssp": (ctypes.c_int, [c_vp, c_i64, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "bcs_shatter": (ctypes.c_int, [c_vp, c_vp, ctypes.POINTER(c_vp)]),
     "bcs_components_get": (ctypes.c_int, [c_vp, ctypes.POINTER(ComponentsView)]),

@@ -5,6 +5,8 @@
 #include <mutex>
 #include <new>
 #include <set>
+#include <cstdio>
+#include <cstdlib>
 
 #include "common.h"
 
@@ -32,6 +34,34 @@ double StageTimer::stop_ms() {
   cudaEventSynchronize(b);
   cudaEventElapsedTime(&ms, a, b);
   return (double)ms;
+}
+
+Tracer::Tracer(const char *scope_name, cudaStream_t stream)
+    : scope(scope_name), s(stream), on(std::getenv("BCS_TRACE") != nullptr) {
+  mark("start");
+}
+
+void Tracer::mark(const char *name) {
+  if (!on) return;
+  cudaEvent_t e;
+  if (cudaEventCreate(&e) != cudaSuccess) return;
+  cudaEventRecord(e, s);
+  marks.emplace_back(name, e);
+}
+
+Tracer::~Tracer() {
+  if (!on || marks.empty()) return;
+  cudaEventSynchronize(marks.back().second);
+  std::string line = std::string("[bcs trace] ") + scope + ":";
+  for (size_t i = 1; i < marks.size(); i++) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, marks[i - 1].second, marks[i].second);
+    char buf[96];
+    std::snprintf(buf, sizeof(buf), " %s %.3f", marks[i].first, ms);
+    line += buf;
+  }
+  std::fprintf(stderr, "%s ms\n", line.c_str());
+  for (auto &m : marks) cudaEventDestroy(m.second);
 }
 
 static std::mutex g_pool_mu;
@@ -71,6 +101,8 @@ int make_ctx(const bcs_opts *opts, Ctx *ctx) {
     }
   }
   ctx->stream = opts ? (cudaStream_t)opts->stream : (cudaStream_t)0;
+  const int64_t mw = opts ? opts->max_wait : 0;
+  ctx->max_wait = mw == 0 ? DEFAULT_MAX_WAIT : (mw < 0 ? 0 : mw);
   return BCS_OK;
 }
 
@@ -126,7 +158,8 @@ struct Input {
   DBuf<int32_t> col;
 };
 
-static int upload_and_validate(Ctx &ctx, const bcs_csr *h, Input *in) {
+static int upload_and_validate(Ctx &ctx, const bcs_csr *h, Input *in, const int64_t *batch_off = nullptr,
+                               int64_t batch_count = 0) {
   in->g.n = h->n;
   in->g.nnz = h->nnz;
   if (h->on_device) {
@@ -149,6 +182,13 @@ static int upload_and_validate(Ctx &ctx, const bcs_csr *h, Input *in) {
   DBuf<int> flags;
   BCS_TRY(flags.alloc(1, ctx.stream));
   BCS_TRY(launch_validate(ctx, in->g, flags.p));
+  DBuf<int64_t> d_off;
+  if (batch_off) {
+    BCS_TRY(d_off.alloc(batch_count + 1, ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(d_off.p, batch_off, (batch_count + 1) * sizeof(int64_t), cudaMemcpyHostToDevice,
+                             ctx.stream));
+    BCS_TRY(launch_validate_batch(ctx, in->g, d_off.p, batch_count, flags.p));
+  }
   int f = 0;
   BCS_CUDA(cudaMemcpyAsync(&f, flags.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
   BCS_CUDA(cudaStreamSynchronize(ctx.stream));
@@ -159,6 +199,7 @@ static int upload_and_validate(Ctx &ctx, const bcs_csr *h, Input *in) {
     if (f & 2) m += " self-loop;";
     if (f & 4) m += " row not strictly ascending (unsorted or duplicate entry);";
     if (f & 8) m += " not symmetric;";
+    if (f & 16) m += " an edge joins two graphs of the batch;";
     set_error(m);
     return BCS_EINVAL;
   }
@@ -297,9 +338,10 @@ static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t st
   return BCS_OK;
 }
 
-static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double *bc_out) {
+static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double *bc_out,
+                          const int64_t *batch_off = nullptr, int64_t batch_count = 0) {
   Input in;
-  BCS_TRY(upload_and_validate(ctx, h, &in));
+  BCS_TRY(upload_and_validate(ctx, h, &in, batch_off, batch_count));
   const uint32_t steps = o ? o->steps : BCS_STEPS_ALL;
   Shattered S;
   BCS_TRY(shatter_impl(ctx, h, in, steps, &S));
@@ -397,6 +439,36 @@ __attribute__((visibility("default"))) int bcs_bc_shattered(const bcs_csr *csr, 
     return BCS_EINVAL;
   }
   return guarded(opts, [&](Ctx &ctx) { return shattered_impl(ctx, csr, opts, bc_out); });
+}
+
+__attribute__((visibility("default"))) int bcs_bc_shattered_batch(const int64_t *graph_vtx_off, int64_t count,
+                                                                  const bcs_csr *packed, const bcs_opts *opts,
+                                                                  double *bc_out) {
+  int rc = check_csr(packed);
+  if (rc != BCS_OK) return rc;
+  if (count < 1 || !graph_vtx_off) {
+    set_error("a batch needs count >= 1 graphs and their vertex offsets");
+    return BCS_EINVAL;
+  }
+  if (graph_vtx_off[0] != 0 || graph_vtx_off[count] != packed->n) {
+    set_error("graph_vtx_off must start at 0 and end at n");
+    return BCS_EINVAL;
+  }
+  for (int64_t g = 0; g < count; g++)
+    if (graph_vtx_off[g + 1] < graph_vtx_off[g]) {
+      set_error("graph_vtx_off must be ascending");
+      return BCS_EINVAL;
+    }
+  if (opts && (opts->steps & ~BCS_STEPS_ALL)) {
+    set_error("unknown bits in opts->steps");
+    return BCS_EINVAL;
+  }
+  if (packed->n == 0) return BCS_OK;
+  if (!bc_out) {
+    set_error("bc_out is NULL");
+    return BCS_EINVAL;
+  }
+  return guarded(opts, [&](Ctx &ctx) { return shattered_impl(ctx, packed, opts, bc_out, graph_vtx_off, count); });
 }
 
 __attribute__((visibility("default"))) int bcs_bc_sources(const bcs_csr *csr, const int64_t *src, int64_t k,

@@ -1,0 +1,55 @@
+// bc_math.cuh - device arithmetic shared by the Bc-Reach kernels.
+#pragma once
+#include <stdint.h>
+
+namespace bcs {
+
+struct Coef32 {
+  float c;
+  int32_t e;
+};
+
+// error flags written by the kernels
+constexpr int ERR_OVERFLOW = 1;  // path counts left the range one BFS level can scale
+constexpr int ERR_DEPTH = 2;     // a multi-source batch needed more BFS levels than it can index
+constexpr int ERR_TIMEOUT = 4;   // a bounded device-side wait ran out
+
+// Binary exponent of a positive double and its [1,2) mantissa as FP32,
+// straight from the bit pattern (no FP64 instruction).  Only the rare
+// subnormal input takes the library route.
+__device__ __forceinline__ void split_pow2(double x, int &e, float &m) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex != 0) {
+    e = ex - 1023;
+    m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));
+  } else {
+    e = ilogb(x);
+    m = (float)scalbn(x, -e);
+  }
+}
+
+// 1/x for a positive double: Newton-Raphson iteration r <- r + r(1 - m r)
+// on the mantissa m in [1,2), seeded by the FP32 hardware reciprocal
+// approximation (relative error ~2^-23, so two steps reach FP64 precision),
+// then the exponent is put back by integer arithmetic on the bit pattern.
+// Inputs here are path counts scaled into [2^-900, 2^960], far from the
+// subnormal and overflow ends; anything else takes the IEEE division.
+__device__ __forceinline__ double recip_pos(double x) {
+  const long long b = __double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (ex < 64 || ex > 2000) return 1.0 / x;
+  const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  float rf;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff))));
+  const int fb = __float_as_int(rf);  // rf in (0.5, 1]: widen to FP64 through the bits
+  double r = __longlong_as_double(((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
+                                  ((long long)(fb & 0x7fffff) << 29));
+  double e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  e = fma(-m, r, 1.0);
+  r = fma(r, e, r);
+  return __longlong_as_double(__double_as_longlong(r) - ((long long)(ex - 1023) << 52));
+}
+
+}  // namespace bcs

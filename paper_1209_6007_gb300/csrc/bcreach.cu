@@ -27,8 +27,11 @@
 // sigma's full range is kept without FP64 arithmetic in phase 2.
 #include <algorithm>
 #include <cfloat>
+#include <cstdlib>
+#include <cstring>
 #include <numeric>
 
+#include "bc_math.cuh"
 #include "common.h"
 
 namespace bcs {
@@ -43,14 +46,6 @@ struct SmallItem {
   int32_t s_end;
   int32_t ngroups;  // groups per CTA (1, 2, 4, 8)
 };
-
-struct Coef32 {
-  float c;
-  int32_t e;
-};
-
-// error flags written by the kernels
-constexpr int ERR_OVERFLOW = 1;
 
 // ------------------------------------------------------------------ group
 struct Group {
@@ -74,44 +69,6 @@ __device__ __forceinline__ double group_max(const Group &g, double x, volatile d
 }
 
 __device__ __forceinline__ int vld(const int32_t *p) { return *(volatile const int32_t *)p; }
-
-// Binary exponent of a positive double and its [1,2) mantissa as FP32,
-// straight from the bit pattern (no FP64 instruction).  Only the rare
-// subnormal input takes the library route.
-__device__ __forceinline__ void split_pow2(double x, int &e, float &m) {
-  const long long b = __double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7ff);
-  if (ex != 0) {
-    e = ex - 1023;
-    m = __int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff));
-  } else {
-    e = ilogb(x);
-    m = (float)scalbn(x, -e);
-  }
-}
-
-// 1/x for a positive double: Newton-Raphson iteration r <- r + r(1 - m r)
-// on the mantissa m in [1,2), seeded by the FP32 hardware reciprocal
-// approximation (relative error ~2^-23, so two steps reach FP64 precision),
-// then the exponent is put back by integer arithmetic on the bit pattern.
-// Inputs here are path counts scaled into [2^-900, 2^960], far from the
-// subnormal and overflow ends; anything else takes the IEEE division.
-__device__ __forceinline__ double recip_pos(double x) {
-  const long long b = __double_as_longlong(x);
-  const int ex = (int)((b >> 52) & 0x7ff);
-  if (ex < 64 || ex > 2000) return 1.0 / x;
-  const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
-  float rf;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rf) : "f"(__int_as_float(0x3f800000 | (int)((b >> 29) & 0x7fffff))));
-  const int fb = __float_as_int(rf);  // rf in (0.5, 1]: widen to FP64 through the bits
-  double r = __longlong_as_double(((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
-                                  ((long long)(fb & 0x7fffff) << 29));
-  double e = fma(-m, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-m, r, 1.0);
-  r = fma(r, e, r);
-  return __longlong_as_double(__double_as_longlong(r) - ((long long)(ex - 1023) << 52));
-}
 
 template <bool FP32>
 struct CoefT;
@@ -138,8 +95,10 @@ struct SrcState {
 };
 
 struct Weights {
-  const int32_t *reach;  // local, nullable
-  const int32_t *ident;  // local, nullable
+  const int32_t *reach;   // local, nullable
+  const int32_t *ident;   // local, nullable
+  const double *init_d;   // reach - 1 as FP64, nullable (converted on the fly)
+  const double *ident_d;  // ident as FP64, nullable
 };
 
 struct Debug {
@@ -149,11 +108,27 @@ struct Debug {
   double *delta;
 };
 
+// Integer part of a 64-bit path count: binary exponent and [1,2) mantissa
+// as FP32 (integer instructions only); x >= 1.
+__device__ __forceinline__ void split_pow2_i64(long long x, int &e, float &m) {
+  e = 63 - __clzll(x);
+  const unsigned long long u = (unsigned long long)x;
+  const unsigned long long mant = e >= 23 ? (u >> (e - 23)) : (u << (23 - e));
+  m = __int_as_float(0x3f800000 | (int)(mant & 0x7fffffull));
+}
+
 // One source of Bc-Reach over a component held as (row, col) with local ids.
-// RESET_BY_QUEUE: the state arrays start as d = -1, sigma = 0 and are put
-// back that way through the queue at the end (global-memory path); else they
-// are initialised here (shared-memory path).  acc is private to the group
-// (plain adds).  dag counts the shortest-path DAG edges seen in phase 2.
+// RESET_BY_QUEUE: the distances start at -1 and are put back that way
+// through the queue at the end (global-memory path); else they are
+// initialised here (shared-memory path).  acc is private to the group (plain
+// adds).  dag counts the shortest-path DAG edges seen in phase 2.
+//
+// Path counts are integers.  While the growth bound fan^L of a level stays
+// below 2^62 they are summed as exact 64-bit integers (the FP64 pipe is the
+// scarce one on GB300, and below 2^53 the values are the same bits as an
+// FP64 sum); the first level whose bound could pass 2^62 converts the level
+// before it to FP64 once, and from there on counts are FP64 with a
+// power-of-two exponent per level.  sig holds int64 on the integer levels.
 template <bool REACH, bool IDENT, bool FP32, bool RESET_BY_QUEUE, typename RowT, typename ColT>
 __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n, const RowT *__restrict__ row,
                                const ColT *__restrict__ col, const Weights wt, const SrcState<FP32> st,
@@ -161,15 +136,17 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
                                unsigned long long &dag) {
   int32_t *const d = st.d;
   double *const sig = st.sig;
+  long long *const sigi = (long long *)st.sig;
   double *const sk = (double *)st.coef;  // sigma[v] * (v == s ? 1 : ident[v]) during phase 1
+  long long *const ski = (long long *)st.coef;
   if (!RESET_BY_QUEUE) {
     for (int v = g.rank; v < n; v += g.size) d[v] = -1;
     g.sync();
   }
   if (g.rank == 0) {
     d[s] = 0;
-    sig[s] = 1.0;
-    sk[s] = 1.0;
+    sigi[s] = 1;
+    ski[s] = 1;
     st.queue[0] = s;
     *st.qtail = 1;
     st.lvl_start[0] = 0;
@@ -179,6 +156,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   g.sync();
   // ---------------------------------------------------------- phase 1
   int lo = 0, hi = 1, L = 0, ecur = 0;
+  int lint = 1 << 30;  // first FP64 level
   double bound = 1.0;
   for (;;) {
     // discover level L+1 (integer work only)
@@ -194,38 +172,61 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
     const int nhi = vld(st.qtail);
     g.sync();
     if (nhi == hi) break;
-    // path counts of level L+1, pulled from level L (one add per DAG edge)
-    for (int i = hi + g.rank; i < nhi; i += g.size) {
-      const int32_t w = st.queue[i];
-      double a = 0.0;
-      const RowT eb = row[w], ee = row[w + 1];
-      for (RowT e = eb; e < ee; e++) {
-        const int32_t u = (int32_t)col[e];
-        if (d[u] == L) a += IDENT ? sk[u] : sig[u];
-      }
-      sig[w] = a;
-      if (IDENT) sk[w] = a * (double)wt.ident[w];
-    }
     bound *= fan;
-    if (bound > 0x1p900) {
-      g.sync();
-      double m = 0.0;
-      for (int i = hi + g.rank; i < nhi; i += g.size) m = fmax(m, sig[st.queue[i]]);
-      m = group_max(g, m, st.red);
-      if (!(m <= DBL_MAX)) {
-        if (g.rank == 0) atomicOr(err, ERR_OVERFLOW);
-      } else if (m > 0x1p960) {
-        const int k = ilogb(m) - 959;
-        for (int i = hi + g.rank; i < nhi; i += g.size) {
-          const int32_t w = st.queue[i];
-          sig[w] = scalbn(sig[w], -k);
-          if (IDENT) sk[w] = scalbn(sk[w], -k);
-        }
-        m = scalbn(m, -k);
-        ecur += k;
+    if (lint > L + 1 && bound >= 0x1p62) {
+      // level L+1 may not fit 63 bits: level L becomes FP64 once
+      lint = L + 1;
+      for (int i = lo + g.rank; i < hi; i += g.size) {
+        const int32_t v = st.queue[i];
+        sk[v] = (double)ski[v];
       }
-      bound = m;
       g.sync();
+    }
+    // path counts of level L+1, pulled from level L (one add per DAG edge)
+    if (L + 1 < lint) {
+      for (int i = hi + g.rank; i < nhi; i += g.size) {
+        const int32_t w = st.queue[i];
+        long long a = 0;
+        const RowT eb = row[w], ee = row[w + 1];
+        for (RowT e = eb; e < ee; e++) {
+          const int32_t u = (int32_t)col[e];
+          if (d[u] == L) a += ski[u];
+        }
+        sigi[w] = a;
+        ski[w] = IDENT ? a * (long long)wt.ident[w] : a;
+      }
+    } else {
+      for (int i = hi + g.rank; i < nhi; i += g.size) {
+        const int32_t w = st.queue[i];
+        double a = 0.0;
+        const RowT eb = row[w], ee = row[w + 1];
+        for (RowT e = eb; e < ee; e++) {
+          const int32_t u = (int32_t)col[e];
+          if (d[u] == L) a += sk[u];
+        }
+        sig[w] = a;
+        sk[w] = IDENT ? a * (wt.ident_d ? wt.ident_d[w] : (double)wt.ident[w]) : a;
+      }
+      if (bound > 0x1p900) {
+        g.sync();
+        double m = 0.0;
+        for (int i = hi + g.rank; i < nhi; i += g.size) m = fmax(m, sig[st.queue[i]]);
+        m = group_max(g, m, st.red);
+        if (!(m <= DBL_MAX)) {
+          if (g.rank == 0) atomicOr(err, ERR_OVERFLOW);
+        } else if (m > 0x1p960) {
+          const int k = ilogb(m) - 959;
+          for (int i = hi + g.rank; i < nhi; i += g.size) {
+            const int32_t w = st.queue[i];
+            sig[w] = scalbn(sig[w], -k);
+            sk[w] = scalbn(sk[w], -k);
+          }
+          m = scalbn(m, -k);
+          ecur += k;
+        }
+        bound = m;
+        g.sync();
+      }
     }
     lo = hi;
     hi = nhi;
@@ -244,33 +245,43 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
     const int a = st.lvl_start[l], b = st.lvl_start[l + 1];
     const int de = (l < Lmax) ? st.lvl_exp[l] - st.lvl_exp[l + 1] : 0;
     const double scl = de == 0 ? 1.0 : (de < -1070 ? 0.0 : scalbn(1.0, de));
+    const bool is_int = l < lint;
     for (int i = a + g.rank; i < b; i += g.size) {
       const int32_t v = st.queue[i];
-      const double sv = sig[v];
       double dv;
       if (!FP32) {
+        const double sv = is_int ? (double)sigi[v] : sig[v];
         double sum = 0.0;
         if (l < Lmax) {
+          // successors first as a bit mask (integer work), then FP64 adds
+          // only for them: an FP64 warp instruction costs the pipe the same
+          // whatever its active lanes, so the FP64 loop should run as few
+          // iterations as possible (the DAG out-degree, not the degree)
           const RowT eb = row[v], ee = row[v + 1];
-          for (RowT e = eb; e < ee; e++) {
-            const int32_t w = (int32_t)col[e];
-            if (d[w] == l + 1) {
-              sum += ((const double *)st.coef)[w];
-              ndag++;
+          for (RowT e0 = eb; e0 < ee; e0 += 32) {
+            const int cnt = (int)((ee - e0) < 32 ? (ee - e0) : 32);
+            uint32_t mask = 0u;
+            for (int j = 0; j < cnt; j++) mask |= (uint32_t)(d[(int32_t)col[e0 + j]] == l + 1) << j;
+            ndag += __popc(mask);
+            while (mask) {
+              const int j = __ffs(mask) - 1;
+              mask &= mask - 1u;
+              sum += ((const double *)st.coef)[(int32_t)col[e0 + j]];
             }
           }
           if (de != 0) sum *= scl;
         }
-        const double init = REACH ? (double)(wt.reach[v] - 1) : 0.0;
+        const double init = REACH ? (wt.init_d ? wt.init_d[v] : (double)(wt.reach[v] - 1)) : 0.0;
         dv = fma(sv, sum, init);
         if (l > 0) {  // the source's coefficient is never read
-          const double kv = IDENT ? (double)wt.ident[v] : 1.0;
+          const double kv = IDENT ? (wt.ident_d ? wt.ident_d[v] : (double)wt.ident[v]) : 1.0;
           ((double *)st.coef)[v] = fma(kv, dv, kv) * recip_pos(sv);
         }
       } else {
         int ev;
         float mv;
-        split_pow2(sv, ev, mv);
+        if (is_int) split_pow2_i64(sigi[v], ev, mv);
+        else split_pow2(sig[v], ev, mv);
         ev += st.lvl_exp[l];
         float sum = 0.0f;
         if (l < Lmax) {
@@ -295,7 +306,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
           ((Coef32 *)st.coef)[v] = cv;
         }
       }
-      if (v != s && dv != 0.0) acc[v] = fma(Ws, dv, acc[v]);
+      if (v != s) acc[v] = fma(Ws, dv, acc[v]);
       if (dbg) dbg->delta[v] = dv;
     }
     g.sync();
@@ -304,18 +315,15 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   if (dbg) {
     for (int i = g.rank; i < hi; i += g.size) {
       const int32_t v = st.queue[i];
-      dbg->d[v] = d[v];
-      dbg->sig[v] = sig[v];
-      dbg->exp[v] = st.lvl_exp[d[v]];
+      const int lv = d[v];
+      dbg->d[v] = lv;
+      dbg->sig[v] = lv < lint ? (double)sigi[v] : sig[v];
+      dbg->exp[v] = st.lvl_exp[lv];
     }
     g.sync();
   }
   if (RESET_BY_QUEUE) {
-    for (int i = g.rank; i < hi; i += g.size) {
-      const int32_t v = st.queue[i];
-      d[v] = -1;
-      sig[v] = 0.0;
-    }
+    for (int i = g.rank; i < hi; i += g.size) d[st.queue[i]] = -1;
     g.sync();
   }
 }
@@ -332,8 +340,8 @@ __host__ __device__ inline size_t small_group_bytes(int64_t n) {
 // distances, queue, path counts, coefficients and its own bc accumulator
 __host__ __device__ inline size_t small_smem_bytes(int64_t n, int64_t nnz, int ng, bool reach, bool ident) {
   size_t b = align16((size_t)(n + 1) * 4) + align16((size_t)nnz * 4);
-  if (reach) b += align16((size_t)n * 4);
-  if (ident) b += align16((size_t)n * 4);
+  if (reach) b += align16((size_t)n * 4) + align16((size_t)n * 8);
+  if (ident) b += align16((size_t)n * 4) + align16((size_t)n * 8);
   return b + small_group_bytes(n) * (size_t)ng;
 }
 
@@ -366,21 +374,32 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     int32_t *col = (int32_t *)p;
     p += align16((size_t)nnz * 4);
     int32_t *reach = nullptr, *ident = nullptr;
+    double *init_d = nullptr, *ident_d = nullptr;
     if (REACH) {
       reach = (int32_t *)p;
       p += align16((size_t)n * 4);
+      init_d = (double *)p;
+      p += align16((size_t)n * 8);
     }
     if (IDENT) {
       ident = (int32_t *)p;
       p += align16((size_t)n * 4);
+      ident_d = (double *)p;
+      p += align16((size_t)n * 8);
     }
     const size_t per = small_group_bytes(n);
     const int64_t r0 = g_row[c.row_off];
     for (int v = tid; v <= n; v += SMALL_THREADS) row[v] = (int32_t)(g_row[c.row_off + v] - r0);
     for (int e = tid; e < nnz; e += SMALL_THREADS) col[e] = g_col[r0 + e];
     for (int v = tid; v < n; v += SMALL_THREADS) {
-      if (REACH) reach[v] = g_reach[c.vtx_off + v];
-      if (IDENT) ident[v] = g_ident[c.vtx_off + v];
+      if (REACH) {
+        reach[v] = g_reach[c.vtx_off + v];
+        init_d[v] = (double)(reach[v] - 1);
+      }
+      if (IDENT) {
+        ident[v] = g_ident[c.vtx_off + v];
+        ident_d[v] = (double)ident[v];
+      }
     }
     // zero every group's accumulator
     for (int x = tid; x < ng * n; x += SMALL_THREADS) {
@@ -408,7 +427,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.lvl_exp = lv + lvl_stride;
     st.qtail = &s_qtail[gid];
     st.red = s_red[gid];
-    Weights wt{reach, ident};
+    Weights wt{reach, ident, init_d, ident_d};
     for (int i = item.s_begin + gid; i < item.s_end; i += ng) {
       const int32_t s = srcs ? (int32_t)srcs[i] : i;
       bcreach_source<REACH, IDENT, FP32, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr, dag);
@@ -485,7 +504,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
     cur = next;
     if (next < 0) break;
     const CompDesc c = comps[cur];
-    Weights wt{REACH ? g_reach + c.vtx_off : nullptr, IDENT ? g_ident + c.vtx_off : nullptr};
+    Weights wt{REACH ? g_reach + c.vtx_off : nullptr, IDENT ? g_ident + c.vtx_off : nullptr, nullptr, nullptr};
     bcreach_source<REACH, IDENT, FP32, true>(g, work[idx].s, c.n, g_row + c.row_off, g_col, wt, st, acc, c.fan, err,
                                              use_dbg ? &dbg_in : nullptr, dag);
   }
@@ -544,6 +563,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   }
   std::vector<SmallItem> items;
   std::vector<LargeSrc> work;
+  std::vector<int32_t> large;
   int64_t nmax_large = 0, nmax_small = 0;
   double total_small_cost = 0.0;
   std::vector<int> ng_of(C, 0);
@@ -584,19 +604,42 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
       for (int64_t b = 0; b < ns; b += chunk)
         items.push_back(SmallItem{(int32_t)ci, (int32_t)b, (int32_t)std::min<int64_t>(ns, b + chunk), ng});
     } else {
-      for (int64_t i = 0; i < ns; i++)
-        work.push_back(LargeSrc{(int32_t)ci, (int32_t)(po.sources ? po.sources[i] : i)});
+      large.push_back((int32_t)ci);
     }
   }
+  // Large pieces: 32 sources per CTA when there are enough batches to give
+  // every SM two of them, else one source per CTA (more CTAs in flight).
+  // BCS_LARGE_PATH=batched|per_source overrides the choice.
+  int64_t nbatches = 0;
+  for (int32_t ci : large) nbatches += ((po.sources ? po.nsources : comps[ci].n) + 31) / 32;
+  bool use_ms = !large.empty() && !dbg && !po.per_source_large && nbatches >= 2 * (int64_t)ctx.num_sms;
+  if (!large.empty() && !dbg && !po.per_source_large) {
+    if (const char *e = std::getenv("BCS_LARGE_PATH")) {
+      if (!std::strcmp(e, "batched")) use_ms = true;
+      if (!std::strcmp(e, "per_source")) use_ms = false;
+    }
+  }
+  // the one-source-per-CTA list for large pieces (debug output, or the
+  // fallback when a graph is too deep for the 32-source kernel)
+  auto build_work = [&]() {
+    work.clear();
+    for (int32_t ci : large) {
+      const int64_t ns = po.sources ? po.nsources : comps[ci].n;
+      for (int64_t i = 0; i < ns; i++)
+        work.push_back(LargeSrc{ci, (int32_t)(po.sources ? po.sources[i] : i)});
+    }
+  };
+  if (!use_ms) build_work();
   // biggest per-source cost first
   std::stable_sort(items.begin(), items.end(), [&](const SmallItem &a, const SmallItem &b) {
     return comps[a.comp].nnz + comps[a.comp].n > comps[b.comp].nnz + comps[b.comp].n;
   });
   ctx.stats.n_small_items = (int64_t)items.size();
-  ctx.stats.n_large_sources = (int64_t)work.size();
+  ctx.stats.n_large_sources = 0;
+  for (int32_t ci : large) ctx.stats.n_large_sources += po.sources ? po.nsources : comps[ci].n;
   ctx.stats.work_sources_entries = work_se;
   ctx.stats.work_sources_vertices = work_sv;
-  if (items.empty() && work.empty()) return BCS_OK;
+  if (items.empty() && large.empty()) return BCS_OK;
 
   DBuf<CompDesc> d_comps;
   DBuf<int> d_err;
@@ -627,6 +670,14 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     BCS_TRY(BCS_DISPATCH3(launch_small_t, R, I, F, ctx, grid, SMALL_SMEM, d_items.p, (int)items.size(), d_err.p + 1,
                           d_comps.p, in, po.sources ? d_srcs.p : nullptr, lvl.p, lvl_stride, d_err.p, d_dag.p));
     ctx.stats.ms_bcreach_small += tm.stop_ms();
+  }
+  if (use_ms) {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    bool depth_failed = false;
+    BCS_TRY(run_ms(ctx, comps, large, in, F, po.sources, po.nsources, d_comps.p, d_err.p, d_dag.p, &depth_failed));
+    if (depth_failed) build_work();
+    ctx.stats.ms_bcreach_large += tm.stop_ms();
   }
   if (!work.empty()) {
     StageTimer tm(ctx.stream);

@@ -35,6 +35,7 @@
 // ascending original id.
 #include <algorithm>
 
+#include "bc_math.cuh"
 #include "common.h"
 #include "uf.cuh"
 
@@ -94,100 +95,166 @@ __global__ void k_bfs_init(int64_t n, const int32_t *__restrict__ adeg, const in
   }
 }
 
-__global__ void k_bfs_expand(int64_t lo, int64_t hi, const int32_t *__restrict__ order_in, const int64_t *__restrict__ rp,
-                             const int32_t *__restrict__ col, const uint8_t *__restrict__ alive, int32_t *level,
-                             int32_t L, int32_t *order_out, unsigned long long *tail) {
-  GRID_STRIDE(i, hi - lo) {
-    const int32_t v = order_in[lo + i];
-    for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
-      const int32_t w = col[k];
-      if (!alive[w] || uf_vload(level + w) >= 0) continue;
-      if (atomicCAS(level + w, -1, L + 1) == -1) push_aggr(order_out, tail, w);
-    }
-  }
+__device__ __forceinline__ bool is_tree_edge(const int32_t *parent, int32_t u, int32_t w) {
+  return parent[w] == u || parent[u] == w;
 }
 
-// parent = smallest-id neighbour on the previous level
-__global__ void k_bfs_parent(int64_t lo, int64_t hi, const int32_t *__restrict__ order, const int64_t *__restrict__ rp,
-                             const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
-                             const int32_t *__restrict__ level, int32_t L, int32_t *parent) {
-  GRID_STRIDE(i, hi - lo) {
-    const int32_t w = order[lo + i];
-    int32_t p = INT32_MAX;
-    for (int64_t k = rp[w]; k < rp[w + 1]; k++) {
-      const int32_t v = col[k];
-      if (alive[v] && level[v] == L && v < p) p = v;
+// ------------------------------------------------ grid barrier (bounded)
+// Sense-reversing barrier over all CTAs of a cooperative launch (which
+// guarantees they are co-resident).  Each wait polls at most `limit` times;
+// a CTA that runs out, or that sees another CTA's error, sets ERR_TIMEOUT
+// and the kernel returns, so no wait is unbounded.
+struct GridBarrier {
+  unsigned int *count;
+  unsigned int *gen;
+  int *err;
+  long long limit;
+};
+
+__device__ bool grid_wait(const GridBarrier &b) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int g = *(volatile unsigned int *)b.gen;
+    __threadfence();
+    if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
+      *(volatile unsigned int *)b.count = 0u;
+      __threadfence();
+      atomicAdd(b.gen, 1u);
+    } else {
+      long long polls = 0;
+      while (*(volatile unsigned int *)b.gen == g) {
+        if (polls++ >= b.limit || *(volatile int *)b.err) {
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
     }
-    parent[w] = p;
+    __threadfence();
+    if (!ok) atomicOr(b.err, ERR_TIMEOUT);
+    s_ok = ok;
   }
+  __syncthreads();
+  return s_ok != 0;
 }
 
-__global__ void k_tree_init(int64_t cnt, const int32_t *__restrict__ order, const int32_t *__restrict__ reach,
-                            int32_t *nd, int64_t *subR, int32_t *pre) {
-  GRID_STRIDE(i, cnt) {
+constexpr int FOREST_THREADS = 1024;
+
+#define COOP_STRIDE(i, lo, hi) \
+  for (int64_t i = (lo) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (hi); i += (int64_t)gridDim.x * blockDim.x)
+
+// The whole spanning-forest pass in one cooperative launch: BFS levels
+// (roots already queued), then subtree sizes and reach sums bottom-up,
+// preorder top-down, and low/high.  lvl_off[l] is where level l starts in
+// order[]; out[0] = number of levels, out[1] = forest size.
+__global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                              const uint8_t *__restrict__ alive, const int32_t *__restrict__ reach, int32_t *level,
+                              int32_t *parent, int32_t *order, unsigned long long *lcount, int32_t *lvl_off,
+                              int32_t *nd, int64_t *subR, int32_t *pre, int32_t *low, int32_t *high, int32_t *out,
+                              const unsigned long long *nroots, GridBarrier bar) {
+  // lcount[l] counts the vertices discovered on level l (one counter per
+  // level, so reading one level's size never races with the next level's
+  // discovery and a single barrier per level suffices)
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  int64_t lo = 0, hi = (int64_t)*nroots;
+  int L = 0;
+  if (lead) {
+    lvl_off[0] = 0;
+    lvl_off[1] = (int32_t)hi;
+  }
+  for (;;) {
+    COOP_STRIDE(i, lo, hi) {  // discover level L+1
+      const int32_t v = order[i];
+      for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+        const int32_t w = col[k];
+        if (!alive[w] || uf_vload(level + w) >= 0) continue;
+        if (atomicCAS(level + w, -1, L + 1) == -1) {
+          const unsigned mask = __activemask();
+          const int leader = __ffs(mask) - 1;
+          const int ln = threadIdx.x & 31;
+          unsigned long long base = 0;
+          if (ln == leader) base = atomicAdd(lcount + L + 1, (unsigned long long)__popc(mask));
+          base = __shfl_sync(mask, base, leader);
+          order[hi + base + __popc(mask & ((1u << ln) - 1))] = w;
+        }
+      }
+    }
+    if (!grid_wait(bar)) return;
+    const int64_t nhi = hi + (int64_t)*(volatile unsigned long long *)(lcount + L + 1);
+    if (nhi == hi) break;
+    COOP_STRIDE(i, hi, nhi) {  // parent = smallest-id neighbour on level L
+      const int32_t w = order[i];
+      int32_t p = INT32_MAX;
+      for (int64_t k = rp[w]; k < rp[w + 1]; k++) {
+        const int32_t v = col[k];
+        if (alive[v] && level[v] == L && v < p) p = v;
+      }
+      parent[w] = p;
+    }
+    lo = hi;
+    hi = nhi;
+    L++;
+    if (lead) lvl_off[L + 1] = (int32_t)hi;
+  }
+  const int nlev = L + 1;
+  const int64_t cnt = hi;
+  COOP_STRIDE(i, 0, cnt) {
     const int32_t v = order[i];
     nd[v] = 1;
     subR[v] = reach[v];
     pre[v] = 0;
   }
-}
-
-__global__ void k_up_sizes(int64_t lo, int64_t hi, const int32_t *__restrict__ order, const int32_t *__restrict__ parent,
-                           int32_t *nd, int64_t *subR) {
-  GRID_STRIDE(i, hi - lo) {
-    const int32_t v = order[lo + i];
-    const int32_t p = parent[v];
-    atomicAdd(nd + p, nd[v]);
-    atomicAdd((unsigned long long *)(subR + p), (unsigned long long)subR[v]);
+  if (!grid_wait(bar)) return;
+  for (int l = nlev - 1; l >= 1; l--) {  // subtree sizes and reach sums
+    COOP_STRIDE(i, lvl_off[l], lvl_off[l + 1]) {
+      const int32_t v = order[i];
+      const int32_t p = parent[v];
+      atomicAdd(nd + p, nd[v]);
+      atomicAdd((unsigned long long *)(subR + p), (unsigned long long)subR[v]);
+    }
+    if (!grid_wait(bar)) return;
   }
-}
-
-// preorder of v's children, in row order: pre[c] = pre[v] + 1 + sizes of earlier children
-__global__ void k_preorder(int64_t lo, int64_t hi, const int32_t *__restrict__ order, const int64_t *__restrict__ rp,
-                           const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
-                           const int32_t *__restrict__ parent, const int32_t *__restrict__ nd, int32_t *pre) {
-  GRID_STRIDE(i, hi - lo) {
-    const int32_t v = order[lo + i];
-    int32_t acc = pre[v] + 1;
-    for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
-      const int32_t w = col[k];
-      if (alive[w] && parent[w] == v) {
-        pre[w] = acc;
-        acc += nd[w];
+  for (int l = 0; l < nlev - 1; l++) {  // preorder, children in row order
+    COOP_STRIDE(i, lvl_off[l], lvl_off[l + 1]) {
+      const int32_t v = order[i];
+      int32_t acc = pre[v] + 1;
+      for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+        const int32_t w = col[k];
+        if (alive[w] && parent[w] == v) {
+          pre[w] = acc;
+          acc += nd[w];
+        }
       }
     }
+    if (!grid_wait(bar)) return;
   }
-}
-
-__device__ __forceinline__ bool is_tree_edge(const int32_t *parent, int32_t u, int32_t w) {
-  return parent[w] == u || parent[u] == w;
-}
-
-__global__ void k_lowhigh_local(int64_t cnt, const int32_t *__restrict__ order, const int64_t *__restrict__ rp,
-                                const int32_t *__restrict__ col, const uint8_t *__restrict__ alive,
-                                const int32_t *__restrict__ parent, const int32_t *__restrict__ pre, int32_t *low,
-                                int32_t *high) {
-  GRID_STRIDE(i, cnt) {
+  COOP_STRIDE(i, 0, cnt) {  // own pre and the far ends of non-tree edges
     const int32_t u = order[i];
-    int32_t lo = pre[u], hi = pre[u];
+    int32_t a = pre[u], b = pre[u];
     for (int64_t k = rp[u]; k < rp[u + 1]; k++) {
       const int32_t w = col[k];
-      if (!alive[w] || is_tree_edge(parent, u, w)) continue;
-      lo = min(lo, pre[w]);
-      hi = max(hi, pre[w]);
+      if (!alive[w] || parent[w] == u || parent[u] == w) continue;
+      a = min(a, pre[w]);
+      b = max(b, pre[w]);
     }
-    low[u] = lo;
-    high[u] = hi;
+    low[u] = a;
+    high[u] = b;
   }
-}
-
-__global__ void k_up_lowhigh(int64_t lo, int64_t hi, const int32_t *__restrict__ order, const int32_t *__restrict__ parent,
-                             int32_t *low, int32_t *high) {
-  GRID_STRIDE(i, hi - lo) {
-    const int32_t v = order[lo + i];
-    const int32_t p = parent[v];
-    atomicMin(low + p, low[v]);
-    atomicMax(high + p, high[v]);
+  if (!grid_wait(bar)) return;
+  for (int l = nlev - 1; l >= 1; l--) {  // low/high over subtrees
+    COOP_STRIDE(i, lvl_off[l], lvl_off[l + 1]) {
+      const int32_t v = order[i];
+      const int32_t p = parent[v];
+      atomicMin(low + p, low[v]);
+      atomicMax(high + p, high[v]);
+    }
+    if (!grid_wait(bar)) return;
+  }
+  if (lead) {
+    out[0] = nlev;
+    out[1] = (int32_t)cnt;
   }
 }
 
@@ -374,6 +441,7 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
   const int64_t n = g.n;
   const int B = 256;
   const int gv = gridv(n, B, ctx.num_sms * 32);
+  Tracer tr("pieces", ctx.stream);
   DBuf<int32_t> adeg, level, parent, order, bid, home_slot, pre, nd, low, high, uf, blk, root_of, top, top_slot;
   DBuf<int64_t> subR, side, childblk, flag, fscan, bcnt, boff, tot, hflag, hpos;
   BCS_TRY(adeg.alloc(n, ctx.stream));
@@ -402,32 +470,8 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
                                          (unsigned long long *)tot.p);
     ctx.launches += 2;
     BCS_CUDA(cudaGetLastError());
-    int64_t cntv = 0;
-    BCS_TRY(read_i64(ctx, tot.p, &cntv, 1));
-    lvl_off.push_back(0);
-    lvl_off.push_back(cntv);
-    // level-synchronous BFS; the host reads each level's size
-    for (int32_t L = 0;; L++) {
-      const int64_t lo = lvl_off[L], hi = lvl_off[L + 1];
-      if (hi == lo) break;
-      k_bfs_expand<<<gridv(hi - lo, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(
-          lo, hi, order.p, g.rp, g.col, alive, level.p, L, order.p, (unsigned long long *)tot.p);
-      ctx.launches++;
-      BCS_CUDA(cudaGetLastError());
-      int64_t nhi = 0;
-      BCS_TRY(read_i64(ctx, tot.p, &nhi, 1));
-      if (nhi > hi) {
-        k_bfs_parent<<<gridv(nhi - hi, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(hi, nhi, order.p, g.rp, g.col, alive,
-                                                                                 level.p, L, parent.p);
-        ctx.launches++;
-      }
-      lvl_off.push_back(nhi);
-      if (nhi == hi) break;
-    }
-    lvl_off.pop_back();  // last entry repeats the previous one
-    const int nlev = (int)lvl_off.size() - 1;
-    tree_cnt = lvl_off.back();
-    // subtree sizes and reach sums, bottom-up
+  tr.mark("roots");
+    // the spanning forest in one cooperative launch
     BCS_TRY(pre.alloc(n, ctx.stream));
     BCS_TRY(nd.alloc(n, ctx.stream));
     BCS_TRY(subR.alloc(n, ctx.stream));
@@ -435,27 +479,56 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     BCS_TRY(high.alloc(n, ctx.stream));
     BCS_TRY(uf.alloc(n, ctx.stream));
     BCS_TRY(blk.alloc(n, ctx.stream));
+    DBuf<int32_t> lvl_off_d, fout, ferr;
+    DBuf<unsigned int> barw;
+    DBuf<unsigned long long> lcount;
+    BCS_TRY(lvl_off_d.alloc(n + 2, ctx.stream));
+    BCS_TRY(lcount.alloc(n + 2, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(lcount.p, 0, (n + 2) * sizeof(unsigned long long), ctx.stream));
+    BCS_TRY(fout.alloc(2, ctx.stream));
+    BCS_TRY(ferr.alloc(1, ctx.stream));
+    BCS_TRY(barw.alloc(2, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(barw.p, 0, 2 * sizeof(unsigned int), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(ferr.p, 0, sizeof(int32_t), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(fout.p, 0, 2 * sizeof(int32_t), ctx.stream));
+    // one CTA of FOREST_THREADS per SM: few arrivals per grid-wide wait
+    int per_sm = 0;
+    BCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forest_coop, FOREST_THREADS, 0));
+    if (per_sm < 1) {
+      set_error("the spanning-forest kernel cannot be resident");
+      return BCS_ECUDA;
+    }
+    const int coop_grid = ctx.num_sms;
+    GridBarrier gb{barw.p, barw.p + 1, ferr.p, (long long)ctx.max_wait};
+    unsigned long long *lcountp = lcount.p;
+    const unsigned long long *nrootsp = (const unsigned long long *)tot.p;
+    int32_t *lvlp = lvl_off_d.p, *ndp = nd.p, *prep = pre.p, *lowp = low.p, *highp = high.p, *foutp = fout.p;
+    int64_t *subRp = subR.p;
+    int32_t *levelp = level.p, *parentp = parent.p, *orderp = order.p;
+    const int64_t *rpp = g.rp;
+    const int32_t *colp = g.col;
+    const uint8_t *alivep = alive;
+    const int32_t *reachp = reach;
+    void *args[] = {(void *)&rpp,   (void *)&colp,  (void *)&alivep, (void *)&reachp, (void *)&levelp,
+                    (void *)&parentp, (void *)&orderp, (void *)&lcountp, (void *)&lvlp,   (void *)&ndp,
+                    (void *)&subRp, (void *)&prep,  (void *)&lowp,   (void *)&highp,  (void *)&foutp,
+                    (void *)&nrootsp, (void *)&gb};
+    BCS_CUDA(cudaLaunchCooperativeKernel((const void *)k_forest_coop, dim3(coop_grid), dim3(FOREST_THREADS), args, 0,
+                                         ctx.stream));
+    ctx.launches++;
+    int32_t hres[3] = {0, 0, 0};
+    BCS_CUDA(cudaMemcpyAsync(hres, fout.p, 2 * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(hres + 2, ferr.p, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+    if (hres[2] & ERR_TIMEOUT) {
+      set_error("a grid-wide wait of the spanning-forest kernel ran out (opts->max_wait)");
+      return BCS_ETIMEOUT;
+    }
+    const int nlev_h = hres[0];
+    tree_cnt = hres[1];
+    lvl_off.assign(1, (int64_t)nlev_h);  // only the level count is kept on the host
     const int gt = gridv(tree_cnt, B, ctx.num_sms * 32);
-    k_tree_init<<<gt, B, 0, ctx.stream>>>(tree_cnt, order.p, reach, nd.p, subR.p, pre.p);
-    ctx.launches++;
-    for (int L = nlev - 1; L >= 1; L--) {
-      const int64_t lo = lvl_off[L], hi = lvl_off[L + 1];
-      k_up_sizes<<<gridv(hi - lo, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(lo, hi, order.p, parent.p, nd.p, subR.p);
-      ctx.launches++;
-    }
-    for (int L = 0; L < nlev - 1; L++) {
-      const int64_t lo = lvl_off[L], hi = lvl_off[L + 1];
-      k_preorder<<<gridv(hi - lo, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(lo, hi, order.p, g.rp, g.col, alive,
-                                                                           parent.p, nd.p, pre.p);
-      ctx.launches++;
-    }
-    k_lowhigh_local<<<gt, B, 0, ctx.stream>>>(tree_cnt, order.p, g.rp, g.col, alive, parent.p, pre.p, low.p, high.p);
-    ctx.launches++;
-    for (int L = nlev - 1; L >= 1; L--) {
-      const int64_t lo = lvl_off[L], hi = lvl_off[L + 1];
-      k_up_lowhigh<<<gridv(hi - lo, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(lo, hi, order.p, parent.p, low.p, high.p);
-      ctx.launches++;
-    }
+  tr.mark("forest");
     // union-find over tree edges
     k_iota_i32_dev<<<gv, B, 0, ctx.stream>>>(n, uf.p);
     BCS_CUDA(cudaMemsetAsync(flag.p, 0, n * sizeof(int64_t), ctx.stream));
@@ -464,6 +537,7 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     k_tv_finish<<<gt, B, 0, ctx.stream>>>(tree_cnt, order.p, level.p, uf.p, blk.p, flag.p);
     ctx.launches += 3;
     BCS_CUDA(cudaGetLastError());
+  tr.mark("unite");
     BCS_TRY(launch_exclusive_scan(ctx, flag.p, fscan.p, n, tot.p));
     BCS_TRY(read_i64(ctx, tot.p, &nb, 1));
     BCS_TRY(top.alloc(nb, ctx.stream));
@@ -490,6 +564,7 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     ctx.launches++;
     BCS_CUDA(cudaGetLastError());
   }
+  tr.mark("blocks");
   // slots: offsets per piece, then the home copies sorted by (piece, vertex)
   BCS_TRY(out->piece_off.alloc(nb + 1, ctx.stream));
   BCS_TRY(launch_exclusive_scan(ctx, bcnt.p, out->piece_off.p, nb, tot.p));
@@ -512,7 +587,9 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
   ctx.launches++;
   int bits = 1;
   while (bits < 32 && ((int64_t)1 << bits) < nb) bits++;
+  tr.mark("list");
   BCS_TRY(radix_sort_pairs(ctx, keys.p, vals.p, tkeys.p, tvals.p, H, bits));
+  tr.mark("sort");
   BCS_TRY(out->slot_org.alloc(S, ctx.stream));
   BCS_TRY(out->slot_reach.alloc(S, ctx.stream));
   BCS_TRY(out->slot_piece.alloc(S, ctx.stream));
@@ -532,6 +609,7 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
   }
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
+  tr.mark("slots");
   // rows: each vertex's thread walks its input row once per pass
   const int32_t *verts = art ? order.p : vals.p;
   const int64_t nverts = art ? tree_cnt : H;
@@ -553,13 +631,15 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
   k_slot_fill<<<gw, B, 0, ctx.stream>>>(nverts, verts, art, g.rp, g.col, alive, parent.p, level.p, bid.p, home_slot.p,
                                         art ? top_slot.p : nullptr, cursor.p, out->scol.p);
   ctx.launches++;
+  tr.mark("rows");
   BCS_TRY(out->piece_maxdeg.alloc(nb, ctx.stream));
   BCS_CUDA(cudaMemsetAsync(out->piece_maxdeg.p, 0, nb * sizeof(int32_t), ctx.stream));
   k_piece_maxdeg<<<gridv(S, B, ctx.num_sms * 32), B, 0, ctx.stream>>>(S, out->srow.p, out->slot_piece.p,
                                                                       out->piece_maxdeg.p);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
-  ctx.stats.bfs_levels = art ? (int64_t)lvl_off.size() - 1 : 0;
+  tr.mark("maxdeg");
+  ctx.stats.bfs_levels = art ? lvl_off[0] : 0;
   ctx.stats.n_slots = S;
   return BCS_OK;
 }

@@ -83,7 +83,13 @@ struct Ctx {
   bcs_stats stats{};
   bool timing = true;
   int64_t launches = 0;
+  // spin limit of device-side waits (grid barriers); < 0: give up at once
+  int64_t max_wait = 0;
 };
+
+// Default number of polls (each followed by a short sleep) a device-side
+// wait makes before it gives up and reports BCS_ETIMEOUT (about a second).
+constexpr int64_t DEFAULT_MAX_WAIT = 1 << 24;
 
 int make_ctx(const bcs_opts *opts, Ctx *ctx);
 
@@ -95,6 +101,19 @@ struct StageTimer {
   ~StageTimer();
   void start();
   double stop_ms();  // synchronises on the stop event
+};
+
+// Optional per-stage trace: with the environment variable BCS_TRACE set,
+// marks are CUDA events on the call's stream and the gaps between them are
+// printed to stderr when the tracer goes out of scope.
+struct Tracer {
+  const char *scope;
+  cudaStream_t s;
+  bool on;
+  std::vector<std::pair<const char *, cudaEvent_t>> marks;
+  Tracer(const char *scope_name, cudaStream_t stream);
+  ~Tracer();
+  void mark(const char *name);
 };
 
 // ------------------------------------------------------- graph on device
@@ -152,6 +171,7 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out);
 
 // ------------------------------------------------------- graph kernels
 int launch_validate(Ctx &ctx, const DevGraph &g, int *d_flags);
+int launch_validate_batch(Ctx &ctx, const DevGraph &g, const int64_t *d_vtx_off, int64_t count, int *d_flags);
 int launch_cc(Ctx &ctx, const DevGraph &g, int32_t *d_label, int64_t *d_N);
 int run_peel(Ctx &ctx, const DevGraph &g, const int64_t *d_N, uint8_t *d_alive, int32_t *d_reach,
              int64_t *d_bcpre);
@@ -160,6 +180,7 @@ int launch_mapback(Ctx &ctx, int64_t nslots, const int32_t *slot_org, const int3
                    const double *bcp, double *d_bc);
 int launch_fill_i32(Ctx &ctx, int32_t *p, int64_t n, int32_t v);
 int launch_fill_i64(Ctx &ctx, int64_t *p, int64_t n, int64_t v);
+int launch_add_f64(Ctx &ctx, double *dst, const double *src, int64_t n);
 int launch_exclusive_scan(Ctx &ctx, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total);
 
 // ------------------------------------------------------- Bc-Reach
@@ -187,12 +208,20 @@ struct BcPlanOpts {
   const int64_t *sources = nullptr;  // host; nullable = every vertex
   int64_t nsources = 0;
   bool force_large = false;           // route every piece through the global path
+  bool per_source_large = false;      // large pieces one source per CTA (no 32-source batches)
   // debug output for a single source (large path only)
   int32_t *dbg_d = nullptr;
   double *dbg_sig = nullptr;
   int32_t *dbg_exp = nullptr;
   double *dbg_delta = nullptr;
 };
+
+// Bc-Reach with 32 sources per CTA over the listed (large) components;
+// *depth_failed reports a graph too deep for its level index (nothing is
+// then added to in.bcp).
+int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32_t> &large, const BcInput &in,
+           bool fp32, const int64_t *sources, int64_t nsources, const CompDesc *d_comps, int *d_err,
+           unsigned long long *d_dag, bool *depth_failed);
 
 // Plan and run Bc-Reach over the given components.  comps are host
 // descriptors; their vertex ranges index BcInput's arrays.

@@ -78,6 +78,34 @@ __global__ void k_validate(int64_t n, int64_t nnz, const int64_t *__restrict__ r
   if (lane == 0 && f) atomicOr(flags, f);
 }
 
+// flag 16: an edge joins two graphs of a batch (vertex ranges vtx_off)
+__global__ void k_validate_batch(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                 const int64_t *__restrict__ vtx_off, int64_t count, int *flags) {
+  for (int64_t u = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; u < n; u += (int64_t)gridDim.x * blockDim.x) {
+    int64_t lo = 0, hi = count;  // graph g with vtx_off[g] <= u < vtx_off[g+1]
+    while (hi - lo > 1) {
+      const int64_t mid = (lo + hi) >> 1;
+      if (vtx_off[mid] <= u) lo = mid;
+      else hi = mid;
+    }
+    const int64_t a = vtx_off[lo], b = vtx_off[lo + 1];
+    for (int64_t k = rp[u]; k < rp[u + 1]; k++)
+      if (col[k] < a || col[k] >= b) {
+        atomicOr(flags, 16);
+        break;
+      }
+  }
+}
+
+int launch_validate_batch(Ctx &ctx, const DevGraph &g, const int64_t *d_vtx_off, int64_t count, int *d_flags) {
+  if (g.n == 0) return BCS_OK;
+  k_validate_batch<<<grid_for(g.n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(g.n, g.rp, g.col, d_vtx_off, count,
+                                                                                  d_flags);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
 int launch_validate(Ctx &ctx, const DevGraph &g, int *d_flags) {
   BCS_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int), ctx.stream));
   if (g.n == 0) return BCS_OK;
@@ -95,27 +123,69 @@ __global__ void k_iota(int64_t n, int32_t *p) {
     p[v] = (int32_t)v;
 }
 
-__global__ void k_cc_hook(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                          int32_t *parent) {
+// Connected components follow Afforest (Sutton, Ben-Nun and Barak, 2018):
+// link every vertex to its first R neighbours, compress, find the component
+// that holds most of a fixed sample of vertices, then process the remaining
+// edges only of vertices outside it (an edge into that component is handled
+// from its other end, and edges inside it change nothing).
+constexpr int CC_FIRST = 2;
+constexpr int CC_SAMPLE = 1024;
+
+__global__ void k_cc_link_first(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                                int32_t *parent) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = rp[v], e = min(rp[v + 1], b + CC_FIRST);
+    for (int64_t k = b; k < e; k++) uf_unite(parent, (int32_t)v, col[k]);
+  }
+}
+
+__global__ void k_cc_compress(int64_t n, int32_t *parent) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    parent[v] = uf_find(parent, (int32_t)v);
+}
+
+// one CTA of CC_SAMPLE threads: the most frequent root of a fixed sample
+// (ties to the smallest root)
+__global__ void k_cc_sample(int64_t n, const int32_t *__restrict__ parent, int32_t *dominant) {
+  __shared__ int32_t roots[CC_SAMPLE];
+  __shared__ unsigned long long best;
+  const int t = threadIdx.x;
+  const int64_t v = (int64_t)(((unsigned long long)t * 2654435761ull) % (unsigned long long)n);
+  roots[t] = parent[v];
+  if (t == 0) best = ~0ull;
+  __syncthreads();
+  int c = 0;
+  for (int j = 0; j < CC_SAMPLE; j++) c += roots[j] == roots[t];
+  // larger count first, then the smaller root
+  atomicMin(&best, ((unsigned long long)(CC_SAMPLE - c) << 32) | (unsigned long long)(uint32_t)roots[t]);
+  __syncthreads();
+  if (t == 0) *dominant = (int32_t)(best & 0xffffffffull);
+}
+
+__global__ void k_cc_link_rest(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                               int32_t *parent, const int32_t *__restrict__ dominant) {
   const int lane = threadIdx.x & 31;
   const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int32_t c = *dominant;
   for (int64_t u = warp; u < n; u += nwarps) {
-    const int64_t b = rp[u], e = rp[u + 1];
-    for (int64_t k = b + lane; k < e; k += 32) {
-      const int32_t v = col[k];
-      if (v > u) uf_unite(parent, (int32_t)u, v);
-    }
+    if (uf_find(parent, (int32_t)u) == c) continue;  // warp-uniform: every lane has the same u
+    const int64_t b = rp[u] + CC_FIRST, e = rp[u + 1];
+    for (int64_t k = b + lane; k < e; k += 32) uf_unite(parent, (int32_t)u, col[k]);
   }
 }
 
 // Roots go to a separate array: the path-halving writes of concurrent finds
-// only ever touch `parent`, so a written label is never overwritten.
+// only ever touch `parent`, so a written label is never overwritten.  Lanes
+// with the same root add their count once (a giant component would otherwise
+// take one atomic per vertex on a single address).
 __global__ void k_cc_finish(int64_t n, int32_t *parent, int32_t *label, unsigned long long *cnt) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    int32_t r = uf_find(parent, (int32_t)v);
+    const int32_t r = uf_find(parent, (int32_t)v);
     label[v] = r;
-    atomicAdd(cnt + r, 1ull);
+    const unsigned act = __activemask();
+    const unsigned m = __match_any_sync(act, r);
+    if ((threadIdx.x & 31) == __ffs(m) - 1) atomicAdd(cnt + r, (unsigned long long)__popc(m));
   }
 }
 
@@ -128,18 +198,22 @@ __global__ void k_cc_size(int64_t n, const int32_t *__restrict__ label, const in
 int launch_cc(Ctx &ctx, const DevGraph &g, int32_t *d_label, int64_t *d_N) {
   if (g.n == 0) return BCS_OK;
   DBuf<int64_t> cnt;
-  DBuf<int32_t> parent;
+  DBuf<int32_t> parent, dom;
   BCS_TRY(cnt.alloc(g.n, ctx.stream));
   BCS_TRY(parent.alloc(g.n, ctx.stream));
+  BCS_TRY(dom.alloc(1, ctx.stream));
   BCS_CUDA(cudaMemsetAsync(cnt.p, 0, g.n * sizeof(int64_t), ctx.stream));
   int block = 256;
   int gv = grid_for(g.n, block, ctx.num_sms * 32);
   k_iota<<<gv, block, 0, ctx.stream>>>(g.n, parent.p);
+  k_cc_link_first<<<gv, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p);
+  k_cc_compress<<<gv, block, 0, ctx.stream>>>(g.n, parent.p);
+  k_cc_sample<<<1, CC_SAMPLE, 0, ctx.stream>>>(g.n, parent.p, dom.p);
   int gw = grid_for(g.n * 32, block, ctx.num_sms * 16);
-  k_cc_hook<<<gw, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p);
+  k_cc_link_rest<<<gw, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p, dom.p);
   k_cc_finish<<<gv, block, 0, ctx.stream>>>(g.n, parent.p, d_label, (unsigned long long *)cnt.p);
   k_cc_size<<<gv, block, 0, ctx.stream>>>(g.n, d_label, cnt.p, d_N);
-  ctx.launches += 4;
+  ctx.launches += 7;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;
 }
@@ -307,6 +381,19 @@ __global__ void k_fill_i64(int64_t *p, int64_t n, int64_t v) {
 int launch_fill_i64(Ctx &ctx, int64_t *p, int64_t n, int64_t v) {
   if (n == 0) return BCS_OK;
   k_fill_i64<<<grid_for(n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(p, n, v);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  return BCS_OK;
+}
+
+__global__ void k_add_f64(double *dst, const double *__restrict__ src, int64_t n) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] += src[i];
+}
+
+int launch_add_f64(Ctx &ctx, double *dst, const double *src, int64_t n) {
+  if (n == 0) return BCS_OK;
+  k_add_f64<<<grid_for(n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(dst, src, n);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;

@@ -83,6 +83,16 @@ def test_host_side_argument_checks():
     assert c.n_pieces == 0
 
 
+def test_batch_argument_checks():
+    import paper_1209_6007_gb300 as bcs
+    rp = np.array([0, 1, 2, 2], np.int64)
+    col = np.array([1, 0], np.int32)
+    for off in ([0, 2], [0, 1, 2], [1, 3], [0, 2, 1, 3]):  # must start at 0, end at n, ascend
+        with pytest.raises(bcs.BcsError) as e:
+            bcs.bc_shattered_batch(off, rp, col)
+        assert e.value.code == bcs.BCS_EINVAL
+
+
 @pytest.mark.skipif(cuda_available(), reason="checks the no-device error path")
 def test_no_device_is_reported():
     import paper_1209_6007_gb300 as bcs

@@ -190,6 +190,56 @@ def test_articulation_full_size_sources_vs_oracle(gpu):
     assert rel(got, ref) <= TOL64
 
 
+# ------------------------------------------- 32-source batches, large pieces
+def test_batched_sources_disconnected_and_ragged(gpu):
+    """Pieces too large for shared memory run 32 sources per CTA; a source
+    list of 45 entries (a ragged last batch) with repeats, on a graph with
+    several components (most sources do not reach most vertices)."""
+    g = gg.disjoint_union(gg.config(1), gg.chung_lu(3000, 2.5, 5.0, 3), gg.cycle(700))
+    rng = np.random.default_rng(11)
+    src = np.concatenate([rng.choice(g.n, size=40, replace=False), [5, 5, 9, 9, 2600]])
+    ref = oracle.bc_sources(g, src)
+    for fp32, tol in ((False, TOL64), (True, TOL32)):
+        assert rel(gpu.bc_sources(g.row_ptr, g.col, src, delta_fp32=fp32), ref) <= tol
+    assert rel(gpu.bc_plain(g.row_ptr, g.col), oracle.bc(g)) <= TOL64
+
+
+def test_batched_sources_path_counts_beyond_double(gpu):
+    """Sources at and near the corners of a 700 x 700 grid: path counts reach
+    2^1392, so each (level, source) pair of a batch gets its own exponent."""
+    side = 700
+    g = gg.grid(side, side)
+    src = [0, 1, side, side * side - 1, side * side - 2, (side // 2) * side + side // 2]
+    ref = oracle.bc_sources(g, src)
+    assert rel(gpu.bc_sources(g.row_ptr, g.col, src), ref) <= TOL64
+    assert rel(gpu.bc_sources(g.row_ptr, g.col, src, delta_fp32=True), ref) <= TOL32
+
+
+# ------------------------------------------------------- uneven batches
+def test_uneven_batch_matches_per_graph_oracle(gpu):
+    """Workload 5's generator at small scale: 60 independent Chung-Lu graphs
+    of log-uniform sizes 16..2048 in one packed CSR, one call."""
+    g, off = gg.batch(60, n_min=16, n_max=2048)
+    got = gpu.bc_shattered_batch(off, g.row_ptr, g.col)
+    ref = oracle.bc(g)  # the packed graph is the disjoint union: same per-graph values
+    assert rel(got, ref) <= TOL64
+    for i in (0, 7, 59):  # and each graph on its own
+        a, b = int(off[i]), int(off[i + 1])
+        sub_e = g.edges()
+        sub_e = sub_e[(sub_e[:, 0] >= a) & (sub_e[:, 0] < b)] - a
+        sub = gg.from_edges(b - a, sub_e)
+        assert rel(got[a:b], oracle.bc(sub)) <= TOL64
+    got32 = gpu.bc_shattered_batch(off, g.row_ptr, g.col, delta_fp32=True)
+    assert rel(got32, ref) <= TOL32
+
+
+def test_batch_rejects_crossing_edges(gpu):
+    g = gg.path(6)
+    with pytest.raises(gpu.BcsError) as e:
+        gpu.bc_shattered_batch([0, 3, 6], g.row_ptr, g.col)  # edge 2-3 joins the two graphs
+    assert e.value.code == gpu._lib.BCS_EINVAL
+
+
 # --------------------------------------------------------------- errors
 def test_malformed_inputs_rejected(gpu):
     bad = {
@@ -204,6 +254,18 @@ def test_malformed_inputs_rejected(gpu):
             with pytest.raises(gpu.BcsError) as e:
                 fn(rp, col)
             assert e.value.code == gpu._lib.BCS_EINVAL, name
+
+
+def test_bounded_wait_times_out_and_context_survives(gpu):
+    """The spanning-forest kernel's grid barrier polls a bounded number of
+    times; with max_wait < 0 every wait gives up at once, the call returns
+    ETIMEOUT and the next call on the same context is correct."""
+    g = gg.config(2, scale_pct=2)
+    with pytest.raises(gpu.BcsError) as e:
+        gpu.bc_shattered(g.row_ptr, g.col, max_wait=-1)
+    assert e.value.code == gpu._lib.BCS_ETIMEOUT
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col), ref) <= TOL64
 
 
 def test_degenerate_graphs(gpu):
