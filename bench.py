@@ -213,8 +213,8 @@ def run_ours(args):
     col = torch.from_numpy(g.col).cuda()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        bcs.bc_shattered(rp, col)
+    for _ in range(args.warmup):  # the first call also runs the autotuner
+        bcs.bc_shattered(rp, col, autotune=True)
     torch.cuda.synchronize()
     stage_sum = {}
     launches = 0
@@ -228,7 +228,7 @@ def run_ours(args):
         flush.zero_()  # L2 flush between timed steps (outside the events)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        bc = bcs.bc_shattered(rp, col)
+        bc = bcs.bc_shattered(rp, col, autotune=True)
         ev1.record(stream)
         ev1.synchronize()
         dev_ms += ev0.elapsed_time(ev1)
@@ -251,13 +251,13 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         for _ in range(2):
-            bcs.bc_shattered(g.row_ptr, g.col)
+            bcs.bc_shattered(g.row_ptr, g.col, autotune=True)
         te = 0.0
         for _ in range(args.steps):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            bcs.bc_shattered(g.row_ptr, g.col)
+            bcs.bc_shattered(g.row_ptr, g.col, autotune=True)
             te += time.perf_counter() - t0
         te = max_over_ranks(te, world)
         e2e = {"value": world * nm * args.steps / te / 1e9, "unit": "GTEPS",
@@ -282,9 +282,9 @@ def run_ours(args):
     fp32 = None
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    bcs.bc_shattered(rp, col, delta_fp32=True)
+    bcs.bc_shattered(rp, col, delta_fp32=True, autotune=True)
     ev0.record(stream)
-    b32 = bcs.bc_shattered(rp, col, delta_fp32=True)
+    b32 = bcs.bc_shattered(rp, col, delta_fp32=True, autotune=True)
     ev1.record(stream)
     ev1.synchronize()
     t32 = ev0.elapsed_time(ev1) / 1e3

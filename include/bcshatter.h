@@ -71,8 +71,9 @@ typedef struct bcs_opts {
   uint32_t steps;     /* BCS_STEP_* mask for bcs_bc_shattered / bcs_shatter */
   int32_t delta_fp32; /* 1: dependency recurrence (Eq. 3) in FP32; path counts
                          and the bc sums stay FP64 */
-  int32_t autotune;   /* 1: pick the small-component work split by timing
-                         candidates once per shape and caching the choice */
+  int32_t autotune;   /* 1: pick the shared-memory Bc-Reach work split (how
+                         many sources a CTA runs at once) by timing the
+                         candidates once per shape bucket, then reuse it */
   int32_t device;     /* CUDA device ordinal; -1 = the current device */
   void *stream;       /* cudaStream_t for all device work; NULL = default */
   int64_t max_wait;   /* polls a device-side wait (grid barrier) makes before
@@ -95,6 +96,8 @@ typedef struct bcs_stats {
                               (summed over sources), when counted */
   int64_t n_ms_batches;    /* 32-source batches on the large-piece path */
   int64_t batch_ctas;      /* CTAs of the 32-source launch */
+  int64_t small_ng_cap;    /* most sources one small-path CTA ran at once */
+  int64_t small_smem_budget; /* shared-memory budget per small-path CTA (bytes) */
   double work_nm;          /* sum over pieces of n_c * m_c (m_c undirected) */
   double work_sources_entries; /* sum over processed sources of the piece's CSR entries */
   double work_sources_vertices; /* sum over processed sources of the piece's vertices */

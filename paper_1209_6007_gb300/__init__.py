@@ -48,7 +48,7 @@ def _is_torch(x) -> bool:
 class _Args:
     """Keeps the marshalled buffers alive for the duration of one call."""
 
-    def __init__(self, row_ptr, col, steps=STEPS_ALL, delta_fp32=False, stream=None, max_wait=0):
+    def __init__(self, row_ptr, col, steps=STEPS_ALL, delta_fp32=False, stream=None, max_wait=0, autotune=False):
         self.keep = []
         self.torch = _is_torch(row_ptr)
         self.opts = Opts()
@@ -56,6 +56,7 @@ class _Args:
         self.opts.delta_fp32 = 1 if delta_fp32 else 0
         self.opts.device = -1
         self.opts.max_wait = max_wait
+        self.opts.autotune = 1 if autotune else 0
         if self.torch:
             import torch
             if row_ptr.device.type != "cuda" or col.device.type != "cuda":
@@ -107,13 +108,15 @@ def bc_plain(row_ptr, col=None, *, delta_fp32: bool = False, stream=None):
 
 
 def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool = False, stream=None,
-                 max_wait: int = 0):
+                 max_wait: int = 0, autotune: bool = False):
     """Shattered + compressed BC (Section 3), equal to Eq. 1 on the input.
 
     max_wait bounds the polls of device-side waits (0: default, < 0: give up
-    at once, which makes the call fail with ETIMEOUT; for tests)."""
+    at once, which makes the call fail with ETIMEOUT; for tests).  autotune
+    times the small-piece work splits once per shape bucket and reuses the
+    fastest."""
     rp, cl = _csr_of(row_ptr, col)
-    a = _Args(rp, cl, steps=steps, delta_fp32=delta_fp32, stream=stream, max_wait=max_wait)
+    a = _Args(rp, cl, steps=steps, delta_fp32=delta_fp32, stream=stream, max_wait=max_wait, autotune=autotune)
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_shattered(ctypes.byref(a.csr), ctypes.byref(a.opts), ptr))
     return out

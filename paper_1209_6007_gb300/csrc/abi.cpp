@@ -103,6 +103,7 @@ int make_ctx(const bcs_opts *opts, Ctx *ctx) {
   ctx->stream = opts ? (cudaStream_t)opts->stream : (cudaStream_t)0;
   const int64_t mw = opts ? opts->max_wait : 0;
   ctx->max_wait = mw == 0 ? DEFAULT_MAX_WAIT : (mw < 0 ? 0 : mw);
+  ctx->autotune = opts && opts->autotune;
   return BCS_OK;
 }
 

@@ -28,7 +28,11 @@
 #include <algorithm>
 #include <cfloat>
 #include <cstdlib>
+#include <cmath>
+#include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <numeric>
 
 #include "bc_math.cuh"
@@ -37,6 +41,9 @@
 namespace bcs {
 
 constexpr int SMALL_THREADS = 256;
+// Shared memory one small-path CTA may use: a piece whose state for a single
+// source does not fit goes to the global-memory path.
+constexpr size_t SMALL_SMEM = 100 * 1024;
 constexpr int SMALL_MAX_GROUPS = 8;
 constexpr int LARGE_THREADS = 512;
 
@@ -515,12 +522,22 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
 static size_t large_scratch_bytes(int64_t nmax) { return (size_t)nmax * (4 + 4 + 8 + 8 + 8) + (size_t)(nmax + 2) * 8; }
 
 // ---------------------------------------------------------- host side
+// CTAs of the shared-memory kernel that fit on one SM with `smem` bytes each
+template <bool R, bool I, bool F>
+static int small_ctas_per_sm(size_t smem, int *out) {
+  auto kern = k_bcreach_small<R, I, F>;
+  BCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM));
+  BCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, SMALL_THREADS, smem));
+  if (*out < 1) *out = 1;
+  return BCS_OK;
+}
+
 template <bool R, bool I, bool F>
 static int launch_small_t(Ctx &ctx, int grid, size_t smem, const SmallItem *items, int nitems, int *counter,
                           const CompDesc *comps, const BcInput &in, const int64_t *srcs, int32_t *lvl, int lvl_stride,
                           int *err, unsigned long long *dag) {
   auto kern = k_bcreach_small<R, I, F>;
-  BCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM));
   kern<<<grid, SMALL_THREADS, smem, ctx.stream>>>(items, nitems, counter, comps, in.row, in.col, in.reach, in.ident,
                                                  srcs, in.bcp, lvl, lvl_stride, err, dag);
   ctx.launches++;
@@ -550,8 +567,30 @@ static int launch_large_t(Ctx &ctx, int grid, const LargeSrc *work, int64_t nwor
               : ((F) ? FN<false, false, true>(__VA_ARGS__)          \
                      : FN<false, false, false>(__VA_ARGS__))))
 
-// Shared memory given to each small-path CTA (two CTAs per SM).
-constexpr size_t SMALL_SMEM = 100 * 1024;
+// The small-path work splits the autotuner tries: most sources a CTA runs
+// at once, and the shared-memory budget per CTA (100 KB: 2 CTAs per SM,
+// 72 KB: 3, 54 KB: 4).  The default is the first.
+struct Split {
+  int ng_cap;
+  size_t budget;
+};
+static const Split TUNE_SPLITS[] = {{8, SMALL_SMEM}, {8, 72 * 1024}, {8, 54 * 1024}, {4, SMALL_SMEM}};
+
+// Process-wide cache of the autotuner's choice (index + 1 into TUNE_SPLITS)
+// per shape bucket.
+static std::mutex g_tune_mu;
+static std::map<long long, int> g_tune;
+
+static int tuned_split(long long key) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key);
+  return it == g_tune.end() ? 0 : it->second;
+}
+
+static void remember_split(long long key, int choice) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = choice;
+}
 
 int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po) {
   const bool R = in.reach != nullptr, I = in.ident != nullptr, F = po.fp32_delta;
@@ -563,50 +602,63 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   }
   std::vector<SmallItem> items;
   std::vector<LargeSrc> work;
-  std::vector<int32_t> large;
+  std::vector<int32_t> large, small;
   int64_t nmax_large = 0, nmax_small = 0;
-  double total_small_cost = 0.0;
-  std::vector<int> ng_of(C, 0);
-  for (int64_t ci = 0; ci < C; ci++) {
-    const CompDesc &c = comps[ci];
-    if (c.n < 2) continue;
-    int ng = 0;
-    if (!po.force_large && !dbg) {
-      for (int cand = SMALL_MAX_GROUPS; cand >= 1; cand >>= 1)
-        if (small_smem_bytes(c.n, c.nnz, cand, R, I) <= SMALL_SMEM) {
-          ng = cand;
-          break;
-        }
-    }
-    ng_of[ci] = ng;
-    const int64_t ns = po.sources ? po.nsources : c.n;
-    if (ng) {
-      total_small_cost += (double)ns * (double)(c.nnz + c.n);
-      nmax_small = std::max<int64_t>(nmax_small, c.n);
-    } else {
-      nmax_large = std::max<int64_t>(nmax_large, c.n);
-    }
-  }
-  const int small_ctas = ctx.num_sms * 2;
-  const double target = total_small_cost / (double)(small_ctas * 8) + 1.0;
-  double work_se = 0.0, work_sv = 0.0;
+  double work_se = 0.0, work_sv = 0.0, total_small_cost = 0.0;
   for (int64_t ci = 0; ci < C; ci++) {
     const CompDesc &c = comps[ci];
     if (c.n < 2) continue;
     const int64_t ns = po.sources ? po.nsources : c.n;
     work_se += (double)ns * (double)c.nnz;
     work_sv += (double)ns * (double)c.n;
-    if (ng_of[ci]) {
-      const int ng = ng_of[ci];
-      const double per = (double)(c.nnz + c.n);
-      int64_t chunk = (int64_t)std::max(1.0, target / per);
-      chunk = ((chunk + ng - 1) / ng) * ng;
-      for (int64_t b = 0; b < ns; b += chunk)
-        items.push_back(SmallItem{(int32_t)ci, (int32_t)b, (int32_t)std::min<int64_t>(ns, b + chunk), ng});
+    const bool fits = !po.force_large && !dbg && small_smem_bytes(c.n, c.nnz, 1, R, I) <= SMALL_SMEM;
+    if (fits) {
+      small.push_back((int32_t)ci);
+      total_small_cost += (double)ns * (double)(c.nnz + c.n);
+      nmax_small = std::max<int64_t>(nmax_small, c.n);
     } else {
       large.push_back((int32_t)ci);
+      nmax_large = std::max<int64_t>(nmax_large, c.n);
     }
   }
+  // The small-path work split: a piece runs up to `ng_cap` sources at once
+  // per CTA (the most that fit in SMALL_SMEM); the launch takes exactly the
+  // shared memory its largest item needs, so occupancy follows the plan.
+  // Items of similar cost go first-largest into a persistent queue.
+  auto plan_small = [&](int ng_cap, size_t budget, std::vector<SmallItem> &out, size_t &smem, int &grid) -> int {
+    out.clear();
+    smem = 0;
+    std::vector<int> ngs(small.size());
+    for (size_t k = 0; k < small.size(); k++) {
+      const CompDesc &c = comps[small[k]];
+      int ng = 1;  // a piece that does not fit the budget even alone still runs (up to SMALL_SMEM)
+      for (int cand = ng_cap; cand >= 1; cand >>= 1)
+        if (small_smem_bytes(c.n, c.nnz, cand, R, I) <= budget) {
+          ng = cand;
+          break;
+        }
+      ngs[k] = ng;
+      smem = std::max(smem, small_smem_bytes(c.n, c.nnz, ng, R, I));
+    }
+    int per_sm = 1;
+    BCS_TRY(BCS_DISPATCH3(small_ctas_per_sm, R, I, F, smem, &per_sm));
+    grid = ctx.num_sms * per_sm;
+    const double target = total_small_cost / (double)((int64_t)grid * SMALL_MAX_GROUPS) + 1.0;
+    for (size_t k = 0; k < small.size(); k++) {
+      const CompDesc &c = comps[small[k]];
+      const int ng = ngs[k];
+      const int64_t ns = po.sources ? po.nsources : c.n;
+      int64_t chunk = (int64_t)std::max(1.0, target / (double)(c.nnz + c.n));
+      chunk = ((chunk + ng - 1) / ng) * ng;
+      for (int64_t b = 0; b < ns; b += chunk)
+        out.push_back(SmallItem{small[k], (int32_t)b, (int32_t)std::min<int64_t>(ns, b + chunk), ng});
+    }
+    std::stable_sort(out.begin(), out.end(), [&](const SmallItem &a, const SmallItem &b) {
+      return comps[a.comp].nnz + comps[a.comp].n > comps[b.comp].nnz + comps[b.comp].n;
+    });
+    grid = (int)std::min<int64_t>(grid, (int64_t)out.size());
+    return BCS_OK;
+  };
   // Large pieces: 32 sources per CTA when there are enough batches to give
   // every SM two of them, else one source per CTA (more CTAs in flight).
   // BCS_LARGE_PATH=batched|per_source overrides the choice.
@@ -630,16 +682,17 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     }
   };
   if (!use_ms) build_work();
-  // biggest per-source cost first
-  std::stable_sort(items.begin(), items.end(), [&](const SmallItem &a, const SmallItem &b) {
-    return comps[a.comp].nnz + comps[a.comp].n > comps[b.comp].nnz + comps[b.comp].n;
-  });
+  int ng_cap = SMALL_MAX_GROUPS;
+  size_t budget = SMALL_SMEM;
+  size_t smem_small = 0;
+  int grid_small = 0;
+  if (!small.empty()) BCS_TRY(plan_small(ng_cap, budget, items, smem_small, grid_small));
   ctx.stats.n_small_items = (int64_t)items.size();
   ctx.stats.n_large_sources = 0;
   for (int32_t ci : large) ctx.stats.n_large_sources += po.sources ? po.nsources : comps[ci].n;
   ctx.stats.work_sources_entries = work_se;
   ctx.stats.work_sources_vertices = work_sv;
-  if (items.empty() && large.empty()) return BCS_OK;
+  if (small.empty() && large.empty()) return BCS_OK;
 
   DBuf<CompDesc> d_comps;
   DBuf<int> d_err;
@@ -658,17 +711,65 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   if (!items.empty()) {
     StageTimer tm(ctx.stream);
     tm.start();
-    DBuf<SmallItem> d_items;
-    DBuf<int32_t> lvl;
-    BCS_TRY(d_items.alloc(items.size(), ctx.stream));
-    BCS_CUDA(cudaMemcpyAsync(d_items.p, items.data(), items.size() * sizeof(SmallItem), cudaMemcpyHostToDevice,
-                             ctx.stream));
     const int lvl_stride = (int)nmax_small + 2;
-    const int grid = std::min<int64_t>(small_ctas, (int64_t)items.size());
-    BCS_TRY(lvl.alloc((size_t)grid * SMALL_MAX_GROUPS * lvl_stride * 2, ctx.stream));
-    BCS_CUDA(cudaMemsetAsync(d_err.p + 1, 0, sizeof(int), ctx.stream));
-    BCS_TRY(BCS_DISPATCH3(launch_small_t, R, I, F, ctx, grid, SMALL_SMEM, d_items.p, (int)items.size(), d_err.p + 1,
-                          d_comps.p, in, po.sources ? d_srcs.p : nullptr, lvl.p, lvl_stride, d_err.p, d_dag.p));
+    const size_t grid_cap = (size_t)ctx.num_sms * (SMALL_THREADS * 8 / SMALL_THREADS);  // 8 CTAs/SM at most
+    DBuf<int32_t> lvl;
+    BCS_TRY(lvl.alloc(grid_cap * SMALL_MAX_GROUPS * lvl_stride * 2, ctx.stream));
+    DBuf<SmallItem> d_items;
+    BCS_TRY(d_items.alloc(std::max<size_t>(items.size() * 2, 1), ctx.stream));
+    auto run_small = [&](const std::vector<SmallItem> &its, size_t smem, int grid, double *target) -> int {
+      if (its.size() > d_items.n) BCS_TRY(d_items.alloc(its.size(), ctx.stream));
+      BCS_CUDA(cudaMemcpyAsync(d_items.p, its.data(), its.size() * sizeof(SmallItem), cudaMemcpyHostToDevice,
+                               ctx.stream));
+      BCS_CUDA(cudaMemsetAsync(d_err.p + 1, 0, sizeof(int), ctx.stream));
+      BcInput tin = in;
+      tin.bcp = target;
+      return BCS_DISPATCH3(launch_small_t, R, I, F, ctx, grid, smem, d_items.p, (int)its.size(), d_err.p + 1,
+                           d_comps.p, tin, po.sources ? d_srcs.p : nullptr, lvl.p, lvl_stride, d_err.p, d_dag.p);
+    };
+    if (ctx.autotune) {
+      // tune once per shape bucket: time each split into a scratch
+      // accumulator and keep the fastest
+      const int kb = 64 - __builtin_clzll((unsigned long long)std::max<int64_t>(nmax_small, 1));
+      const int wb = (int)std::log2(std::max(total_small_cost, 1.0));
+      const long long key = ((long long)(R * 4 + I * 2 + F) << 40) | ((long long)kb << 20) | (long long)wb;
+      int best = tuned_split(key);
+      if (best == 0) {
+        int64_t ntot = 0;
+        for (const CompDesc &c : comps) ntot = std::max<int64_t>(ntot, c.vtx_off + c.n);
+        DBuf<double> scratch;
+        BCS_TRY(scratch.alloc(ntot, ctx.stream));
+        double best_ms = 1e30;
+        for (int cand = 0; cand < (int)(sizeof(TUNE_SPLITS) / sizeof(TUNE_SPLITS[0])); cand++) {
+          std::vector<SmallItem> its;
+          size_t sm = 0;
+          int gr = 0;
+          BCS_TRY(plan_small(TUNE_SPLITS[cand].ng_cap, TUNE_SPLITS[cand].budget, its, sm, gr));
+          BCS_CUDA(cudaMemsetAsync(scratch.p, 0, ntot * 8, ctx.stream));
+          StageTimer tt(ctx.stream);
+          tt.start();
+          BCS_TRY(run_small(its, sm, gr, scratch.p));
+          const double ms = tt.stop_ms();
+          if (std::getenv("BCS_TRACE"))
+            std::fprintf(stderr, "[bcs] tune small split ng_cap=%d budget=%zu: %zu items, %d CTAs, %zu B smem, %.3f ms\n",
+                         TUNE_SPLITS[cand].ng_cap, TUNE_SPLITS[cand].budget, its.size(), gr, sm, ms);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = cand + 1;
+          }
+        }
+        BCS_CUDA(cudaMemsetAsync(d_dag.p, 0, sizeof(unsigned long long), ctx.stream));
+        remember_split(key, best);
+      }
+      ng_cap = TUNE_SPLITS[best - 1].ng_cap;
+      budget = TUNE_SPLITS[best - 1].budget;
+      BCS_TRY(plan_small(ng_cap, budget, items, smem_small, grid_small));
+      ctx.stats.n_small_items = (int64_t)items.size();
+      tm.start();
+    }
+    ctx.stats.small_ng_cap = ng_cap;
+    ctx.stats.small_smem_budget = (int64_t)budget;
+    BCS_TRY(run_small(items, smem_small, grid_small, in.bcp));
     ctx.stats.ms_bcreach_small += tm.stop_ms();
   }
   if (use_ms) {

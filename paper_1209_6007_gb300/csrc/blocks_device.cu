@@ -6,7 +6,8 @@
 // Biconnected components follow Tarjan and Vishkin's characterisation over
 // any rooted spanning tree, here a BFS forest (one tree per component, rooted
 // at its smallest live vertex; every vertex takes its smallest-id neighbour of
-// the previous level as parent, so the forest is deterministic):
+// the previous level as parent, so the forest is deterministic; the preorder
+// numbers depend on the order of atomics, the blocks do not):
 //   pre[v]  preorder number, nd[v] subtree size,
 //   low[v]/high[v]  min/max of pre over v's subtree and the far ends of the
 //                   non-tree edges leaving it.
@@ -77,10 +78,18 @@ __global__ void k_alive_deg(int64_t n, const int64_t *__restrict__ rp, const int
   }
 }
 
+// root of each component's tree: its smallest live vertex with a live edge
+// (lanes of a warp with the same label combine first: a giant component
+// would otherwise send one atomic per vertex to a single address)
 __global__ void k_roots(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ label,
                         int32_t *root_of) {
   GRID_STRIDE(v, n) {
-    if (adeg[v] > 0) atomicMin(root_of + label[v], (int32_t)v);
+    if (adeg[v] > 0) {
+      const int32_t l = label[v];
+      const unsigned m = __match_any_sync(__activemask(), l);
+      const int32_t lo = __reduce_min_sync(m, (int32_t)v);
+      if ((int)(threadIdx.x & 31) == __ffs(m) - 1) atomicMin(root_of + l, lo);
+    }
   }
 }
 
@@ -129,7 +138,6 @@ __device__ bool grid_wait(const GridBarrier &b) {
           ok = 0;
           break;
         }
-        __nanosleep(64);
       }
     }
     __threadfence();
@@ -153,7 +161,7 @@ __global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__r
                               const uint8_t *__restrict__ alive, const int32_t *__restrict__ reach, int32_t *level,
                               int32_t *parent, int32_t *order, unsigned long long *lcount, int32_t *lvl_off,
                               int32_t *nd, int64_t *subR, int32_t *pre, int32_t *low, int32_t *high, int32_t *out,
-                              const unsigned long long *nroots, GridBarrier bar) {
+                              const unsigned long long *nroots, int32_t *cursor, GridBarrier bar) {
   // lcount[l] counts the vertices discovered on level l (one counter per
   // level, so reading one level's size never races with the next level's
   // discovery and a single barrier per level suffices)
@@ -205,6 +213,7 @@ __global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__r
     nd[v] = 1;
     subR[v] = reach[v];
     pre[v] = 0;
+    cursor[v] = 0;
   }
   if (!grid_wait(bar)) return;
   for (int l = nlev - 1; l >= 1; l--) {  // subtree sizes and reach sums
@@ -216,17 +225,14 @@ __global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__r
     }
     if (!grid_wait(bar)) return;
   }
-  for (int l = 0; l < nlev - 1; l++) {  // preorder, children in row order
+  // preorder, level by level: each child takes the next free range of its
+  // parent with one atomic (any order of siblings gives contiguous subtree
+  // ranges; the blocks do not depend on it)
+  for (int l = 1; l < nlev; l++) {
     COOP_STRIDE(i, lvl_off[l], lvl_off[l + 1]) {
-      const int32_t v = order[i];
-      int32_t acc = pre[v] + 1;
-      for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
-        const int32_t w = col[k];
-        if (alive[w] && parent[w] == v) {
-          pre[w] = acc;
-          acc += nd[w];
-        }
-      }
+      const int32_t c = order[i];
+      const int32_t p = parent[c];
+      pre[c] = pre[p] + 1 + atomicAdd(cursor + p, nd[c]);
     }
     if (!grid_wait(bar)) return;
   }
@@ -502,6 +508,9 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     GridBarrier gb{barw.p, barw.p + 1, ferr.p, (long long)ctx.max_wait};
     unsigned long long *lcountp = lcount.p;
     const unsigned long long *nrootsp = (const unsigned long long *)tot.p;
+    DBuf<int32_t> cursor;
+    BCS_TRY(cursor.alloc(n, ctx.stream));
+    int32_t *cursorp = cursor.p;
     int32_t *lvlp = lvl_off_d.p, *ndp = nd.p, *prep = pre.p, *lowp = low.p, *highp = high.p, *foutp = fout.p;
     int64_t *subRp = subR.p;
     int32_t *levelp = level.p, *parentp = parent.p, *orderp = order.p;
@@ -512,7 +521,7 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     void *args[] = {(void *)&rpp,   (void *)&colp,  (void *)&alivep, (void *)&reachp, (void *)&levelp,
                     (void *)&parentp, (void *)&orderp, (void *)&lcountp, (void *)&lvlp,   (void *)&ndp,
                     (void *)&subRp, (void *)&prep,  (void *)&lowp,   (void *)&highp,  (void *)&foutp,
-                    (void *)&nrootsp, (void *)&gb};
+                    (void *)&nrootsp, (void *)&cursorp, (void *)&gb};
     BCS_CUDA(cudaLaunchCooperativeKernel((const void *)k_forest_coop, dim3(coop_grid), dim3(FOREST_THREADS), args, 0,
                                          ctx.stream));
     ctx.launches++;

@@ -85,6 +85,7 @@ struct Ctx {
   int64_t launches = 0;
   // spin limit of device-side waits (grid barriers); < 0: give up at once
   int64_t max_wait = 0;
+  bool autotune = false;
 };
 
 // Default number of polls (each followed by a short sleep) a device-side

@@ -171,7 +171,11 @@ __global__ void k_cc_link_rest(int64_t n, const int64_t *__restrict__ rp, const 
   for (int64_t u = warp; u < n; u += nwarps) {
     if (uf_find(parent, (int32_t)u) == c) continue;  // warp-uniform: every lane has the same u
     const int64_t b = rp[u] + CC_FIRST, e = rp[u + 1];
-    for (int64_t k = b + lane; k < e; k += 32) uf_unite(parent, (int32_t)u, col[k]);
+    for (int64_t k = b + lane; k < e; k += 32) {
+      const int32_t v = col[k];
+      // after the compression most linked pairs already share a parent
+      if (uf_vload(parent + u) != uf_vload(parent + v)) uf_unite(parent, (int32_t)u, v);
+    }
   }
 }
 

@@ -118,6 +118,18 @@ def test_shattered_config1(gpu, steps):
     assert rel(gpu.bc_shattered(g.row_ptr, g.col, steps=steps, delta_fp32=True), ref) <= TOL32
 
 
+def test_autotuned_split_gives_the_same_result(gpu):
+    """The autotuner times a few small-path work splits into a scratch
+    accumulator on the first call of a shape bucket, then reuses the pick."""
+    g = gg.config(2, scale_pct=3)
+    ref = oracle.bc(g)
+    for _ in range(2):
+        assert rel(gpu.bc_shattered(g.row_ptr, g.col, autotune=True), ref) <= TOL64
+        st = gpu.last_stats()
+        assert st["small_ng_cap"] in (4, 8)
+        assert st["small_smem_budget"] in (100 * 1024, 72 * 1024, 54 * 1024)
+
+
 def test_shattered_articulation_scaled(gpu):
     """Config 2 at 5% of its blocks: full oracle in seconds, many pieces."""
     g = gg.config(2, scale_pct=5)
