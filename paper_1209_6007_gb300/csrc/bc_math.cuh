@@ -29,10 +29,23 @@ __device__ __forceinline__ void split_pow2(double x, int &e, float &m) {
   }
 }
 
-// 1/x for a positive double: Newton-Raphson iteration r <- r + r(1 - m r)
-// on the mantissa m in [1,2), seeded by the FP32 hardware reciprocal
-// approximation (relative error ~2^-23, so two steps reach FP64 precision),
-// then the exponent is put back by integer arithmetic on the bit pattern.
+// ceil(log2 x) for x >= 1 from the bit pattern (integer instructions only)
+__device__ __forceinline__ int ceil_log2_pos(double x) {
+  const long long b = __double_as_longlong(x);
+  return (int)((b >> 52) & 0x7ff) - 1023 + ((b & 0x000fffffffffffffLL) != 0);
+}
+
+// 2^k as a double for k <= 1023, built from the bits (0 below the normal range)
+__device__ __forceinline__ double pow2_int(int k) {
+  return k < -1022 ? 0.0 : __longlong_as_double((long long)(k + 1023) << 52);
+}
+
+// 1/x for a positive double.  The mantissa m in [1,2) gets an FP32 hardware
+// reciprocal approximation r (relative error e = 1 - m r of about 2^-22),
+// refined by one third-order step of the series 1/m = r (1 + e + e^2 + ...):
+// r <- r + r (e + e^2), leaving an error near e^3 ~ 2^-66, below FP64
+// rounding, in three FMAs.  The exponent is put back by integer arithmetic
+// on the bit pattern.
 // Inputs here are path counts scaled into [2^-900, 2^960], far from the
 // subnormal and overflow ends; anything else takes the IEEE division.
 __device__ __forceinline__ double recip_pos(double x) {
@@ -45,10 +58,8 @@ __device__ __forceinline__ double recip_pos(double x) {
   const int fb = __float_as_int(rf);  // rf in (0.5, 1]: widen to FP64 through the bits
   double r = __longlong_as_double(((long long)(((fb >> 23) & 0xff) - 127 + 1023) << 52) |
                                   ((long long)(fb & 0x7fffff) << 29));
-  double e = fma(-m, r, 1.0);
-  r = fma(r, e, r);
-  e = fma(-m, r, 1.0);
-  r = fma(r, e, r);
+  const double e = fma(-m, r, 1.0);
+  r = fma(r, fma(e, e, e), r);
   return __longlong_as_double(__double_as_longlong(r) - ((long long)(ex - 1023) << 52));
 }
 

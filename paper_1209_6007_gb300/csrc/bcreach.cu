@@ -95,11 +95,13 @@ struct SrcState {
   double *sig;
   typename CoefT<FP32>::type *coef;  // phase 1 keeps sigma * ident here
   int32_t *queue;
+  uint32_t *dmask;     // shared-memory path: DAG successors among the first 32 row entries
   int32_t *lvl_start;  // levels + 2
   int32_t *lvl_exp;    // levels + 1
   int *qtail;          // shared counter
-  double *red;         // shared, 16 doubles
+  double *red;         // shared, 16 doubles: group maxima, and the source weight
 };
+constexpr int RED_WS = 15;  // slot of the source weight in SrcState::red
 
 struct Weights {
   const int32_t *reach;   // local, nullable
@@ -136,6 +138,13 @@ __device__ __forceinline__ void split_pow2_i64(long long x, int &e, float &m) {
 // FP64 sum); the first level whose bound could pass 2^62 converts the level
 // before it to FP64 once, and from there on counts are FP64 with a
 // power-of-two exponent per level.  sig holds int64 on the integer levels.
+//
+// Shared-memory path (!RESET_BY_QUEUE): one pass over a level's rows both
+// discovers the next level and, on the integer levels, pushes the path
+// counts along the DAG edges it finds (64-bit shared-memory atomics); each
+// vertex also keeps the DAG edges among its first 32 row entries as a bit
+// mask, so phase 2 visits only the successors.  The global-memory path
+// pulls the counts in a second pass and finds successors by their level.
 template <bool REACH, bool IDENT, bool FP32, bool RESET_BY_QUEUE, typename RowT, typename ColT>
 __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n, const RowT *__restrict__ row,
                                const ColT *__restrict__ col, const Weights wt, const SrcState<FP32> st,
@@ -146,8 +155,13 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   long long *const sigi = (long long *)st.sig;
   double *const sk = (double *)st.coef;  // sigma[v] * (v == s ? 1 : ident[v]) during phase 1
   long long *const ski = (long long *)st.coef;
+  constexpr bool PUSH = !RESET_BY_QUEUE;
+  long long *const pull_src = IDENT ? ski : sigi;  // sigma * ident (the source counts once)
   if (!RESET_BY_QUEUE) {
-    for (int v = g.rank; v < n; v += g.size) d[v] = -1;
+    for (int v = g.rank; v < n; v += g.size) {
+      d[v] = -1;
+      sigi[v] = 0;
+    }
     g.sync();
   }
   if (g.rank == 0) {
@@ -164,43 +178,71 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   // ---------------------------------------------------------- phase 1
   int lo = 0, hi = 1, L = 0, ecur = 0;
   int lint = 1 << 30;  // first FP64 level
-  double bound = 1.0;
+  // growth bound of the current level's counts as a power of two, kept in
+  // integers: level-uniform FP64 tests would be evaluated by every lane
+  const int flg = ceil_log2_pos(fan);
+  int blg = 0;
   for (;;) {
+    // level L+1 keeps integer counts while its growth bound stays below 2^62
+    const bool push = PUSH && lint > L + 1 && blg + flg < 62;
+    // below 2^31 every partial sum fits the low word: 32-bit atomics
+    const bool push32 = push && blg + flg < 31;
     // discover level L+1 (integer work only)
     for (int i = lo + g.rank; i < hi; i += g.size) {
       const int32_t v = st.queue[i];
       const RowT eb = row[v], ee = row[v + 1];
-      for (RowT e = eb; e < ee; e++) {
-        const int32_t w = (int32_t)col[e];
-        if (vld(d + w) < 0 && atomicCAS(d + w, -1, L + 1) == -1) st.queue[atomicAdd(st.qtail, 1)] = w;
+      if (PUSH) {
+        // sigma[v] * ident[v], formed by v's own lane (sigma[v] is final)
+        const long long pv = !push ? 0 : (IDENT && v != s ? sigi[v] * (long long)wt.ident[v] : sigi[v]);
+        uint32_t m = 0u;
+        for (RowT e = eb; e < ee; e++) {
+          const int32_t w = (int32_t)col[e];
+          int dw = vld(d + w);
+          if (dw < 0) {
+            dw = atomicCAS(d + w, -1, L + 1);
+            if (dw < 0) st.queue[atomicAdd(st.qtail, 1)] = w;
+          }
+          if (dw < 0 || dw == L + 1) {
+            if (push32) atomicAdd((unsigned int *)(sigi + w), (unsigned int)pv);
+            else if (push) atomicAdd((unsigned long long *)(sigi + w), (unsigned long long)pv);
+            if (e - eb < 32) m |= 1u << (int)(e - eb);
+          }
+        }
+        st.dmask[v] = m;
+      } else {
+        for (RowT e = eb; e < ee; e++) {
+          const int32_t w = (int32_t)col[e];
+          if (vld(d + w) < 0 && atomicCAS(d + w, -1, L + 1) == -1) st.queue[atomicAdd(st.qtail, 1)] = w;
+        }
       }
     }
     g.sync();
     const int nhi = vld(st.qtail);
     g.sync();
     if (nhi == hi) break;
-    bound *= fan;
-    if (lint > L + 1 && bound >= 0x1p62) {
+    blg += flg;
+    if (lint > L + 1 && blg >= 62) {
       // level L+1 may not fit 63 bits: level L becomes FP64 once
       lint = L + 1;
       for (int i = lo + g.rank; i < hi; i += g.size) {
         const int32_t v = st.queue[i];
-        sk[v] = (double)ski[v];
+        sk[v] = PUSH ? (double)sigi[v] * (IDENT && v != s ? (double)wt.ident[v] : 1.0) : (double)pull_src[v];
       }
       g.sync();
     }
-    // path counts of level L+1, pulled from level L (one add per DAG edge)
-    if (L + 1 < lint) {
+    if (push) {
+      // the counts of level L+1 are complete
+    } else if (L + 1 < lint) {  // path counts of level L+1, pulled from level L (one add per DAG edge)
       for (int i = hi + g.rank; i < nhi; i += g.size) {
         const int32_t w = st.queue[i];
         long long a = 0;
         const RowT eb = row[w], ee = row[w + 1];
         for (RowT e = eb; e < ee; e++) {
           const int32_t u = (int32_t)col[e];
-          if (d[u] == L) a += ski[u];
+          if (d[u] == L) a += pull_src[u];
         }
         sigi[w] = a;
-        ski[w] = IDENT ? a * (long long)wt.ident[w] : a;
+        if (IDENT) ski[w] = a * (long long)wt.ident[w];
       }
     } else {
       for (int i = hi + g.rank; i < nhi; i += g.size) {
@@ -214,7 +256,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
         sig[w] = a;
         sk[w] = IDENT ? a * (wt.ident_d ? wt.ident_d[w] : (double)wt.ident[w]) : a;
       }
-      if (bound > 0x1p900) {
+      if (blg > 900) {
         g.sync();
         double m = 0.0;
         for (int i = hi + g.rank; i < nhi; i += g.size) m = fmax(m, sig[st.queue[i]]);
@@ -231,7 +273,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
           m = scalbn(m, -k);
           ecur += k;
         }
-        bound = m;
+        blg = m >= 1.0 ? ceil_log2_pos(m) : 0;
         g.sync();
       }
     }
@@ -244,14 +286,17 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
     }
   }
   const int Lmax = L;
+  // the source's weight reach[s] * ident[s] waits in shared memory: read
+  // per vertex, it is never recomputed (FP64) inside the divergent loop
+  if (g.rank == 0)
+    st.red[RED_WS] = (double)((REACH ? (long long)wt.reach[s] : 1ll) * (IDENT ? (long long)wt.ident[s] : 1ll));
   g.sync();
   // ---------------------------------------------------------- phase 2
-  const double Ws = (REACH ? (double)wt.reach[s] : 1.0) * (IDENT ? (double)wt.ident[s] : 1.0);
   unsigned long long ndag = 0;
   for (int l = Lmax; l >= 0; l--) {
     const int a = st.lvl_start[l], b = st.lvl_start[l + 1];
     const int de = (l < Lmax) ? st.lvl_exp[l] - st.lvl_exp[l + 1] : 0;
-    const double scl = de == 0 ? 1.0 : (de < -1070 ? 0.0 : scalbn(1.0, de));
+    const double scl = pow2_int(de);
     const bool is_int = l < lint;
     for (int i = a + g.rank; i < b; i += g.size) {
       const int32_t v = st.queue[i];
@@ -266,9 +311,13 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
           // iterations as possible (the DAG out-degree, not the degree)
           const RowT eb = row[v], ee = row[v + 1];
           for (RowT e0 = eb; e0 < ee; e0 += 32) {
-            const int cnt = (int)((ee - e0) < 32 ? (ee - e0) : 32);
             uint32_t mask = 0u;
-            for (int j = 0; j < cnt; j++) mask |= (uint32_t)(d[(int32_t)col[e0 + j]] == l + 1) << j;
+            if (PUSH && e0 == eb) {
+              mask = st.dmask[v];
+            } else {
+              const int cnt = (int)((ee - e0) < 32 ? (ee - e0) : 32);
+              for (int j = 0; j < cnt; j++) mask |= (uint32_t)(d[(int32_t)col[e0 + j]] == l + 1) << j;
+            }
             ndag += __popc(mask);
             while (mask) {
               const int j = __ffs(mask) - 1;
@@ -293,13 +342,21 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
         float sum = 0.0f;
         if (l < Lmax) {
           const RowT eb = row[v], ee = row[v + 1];
-          for (RowT e = eb; e < ee; e++) {
-            const int32_t w = (int32_t)col[e];
-            if (d[w] == l + 1) {
-              const Coef32 cw = ((const Coef32 *)st.coef)[w];
+          for (RowT e0 = eb; e0 < ee; e0 += 32) {
+            uint32_t mask = 0u;
+            if (PUSH && e0 == eb) {
+              mask = st.dmask[v];
+            } else {
+              const int cnt = (int)((ee - e0) < 32 ? (ee - e0) : 32);
+              for (int j = 0; j < cnt; j++) mask |= (uint32_t)(d[(int32_t)col[e0 + j]] == l + 1) << j;
+            }
+            ndag += __popc(mask);
+            while (mask) {
+              const int j = __ffs(mask) - 1;
+              mask &= mask - 1u;
+              const Coef32 cw = ((const Coef32 *)st.coef)[(int32_t)col[e0 + j]];
               const int x = ev - cw.e;  // <= 0: sigma[v] <= sigma[w]
               if (x >= -126) sum = fmaf(cw.c, __int_as_float((127 + x) << 23), sum);
-              ndag++;
             }
           }
         }
@@ -313,7 +370,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
           ((Coef32 *)st.coef)[v] = cv;
         }
       }
-      if (v != s) acc[v] = fma(Ws, dv, acc[v]);
+      if (v != s) acc[v] = fma(st.red[RED_WS], dv, acc[v]);
       if (dbg) dbg->delta[v] = dv;
     }
     g.sync();
@@ -338,8 +395,10 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
 // ---------------------------------------------------------- small path
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// per group: distances, queue and DAG masks (4 bytes each), path counts,
+// coefficients and the group's bc accumulator (8 bytes each)
 __host__ __device__ inline size_t small_group_bytes(int64_t n) {
-  return align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 3;
+  return align16((size_t)n * 4) * 3 + align16((size_t)n * 8) * 3;
 }
 
 // bytes of shared memory a component needs with `ng` concurrent sources:
@@ -411,7 +470,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     // zero every group's accumulator
     for (int x = tid; x < ng * n; x += SMALL_THREADS) {
       const int gi = x / n, v = x - gi * n;
-      double *a = (double *)(p + per * gi + align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 2);
+      double *a = (double *)(p + per * gi + align16((size_t)n * 4) * 3 + align16((size_t)n * 8) * 2);
       a[v] = 0.0;
     }
     __syncthreads();
@@ -423,6 +482,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.d = (int32_t *)q;
     q += align16((size_t)n * 4);
     st.queue = (int32_t *)q;
+    q += align16((size_t)n * 4);
+    st.dmask = (uint32_t *)q;
     q += align16((size_t)n * 4);
     st.sig = (double *)q;
     q += align16((size_t)n * 8);
@@ -444,7 +505,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     for (int v = tid; v < n; v += SMALL_THREADS) {
       double t = 0.0;
       for (int gi = 0; gi < ng; gi++)
-        t += ((const double *)(p + per * gi + align16((size_t)n * 4) * 2 + align16((size_t)n * 8) * 2))[v];
+        t += ((const double *)(p + per * gi + align16((size_t)n * 4) * 3 + align16((size_t)n * 8) * 2))[v];
       if (t != 0.0) atomicAdd(bcp + c.vtx_off + v, t);
     }
     __syncthreads();
@@ -484,6 +545,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
   SrcState<FP32> st;
   st.d = sc.d + b * sc.nmax;
   st.queue = sc.queue + b * sc.nmax;
+  st.dmask = nullptr;
   st.sig = sc.sig + b * sc.nmax;
   st.coef = (typename CoefT<FP32>::type *)(sc.coef + b * sc.nmax);
   double *acc = sc.acc + b * sc.nmax;

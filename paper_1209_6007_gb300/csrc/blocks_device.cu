@@ -35,9 +35,11 @@
 // copy's row is the matching subsequence of the input row, so rows stay in
 // ascending original id.
 #include <algorithm>
+#include <cstdio>
 
 #include "bc_math.cuh"
 #include "common.h"
+#include "coop.cuh"
 #include "uf.cuh"
 
 namespace bcs {
@@ -97,8 +99,8 @@ __global__ void k_bfs_init(int64_t n, const int32_t *__restrict__ adeg, const in
                            const int32_t *__restrict__ root_of, int32_t *level, int32_t *parent, int32_t *order,
                            unsigned long long *tail) {
   GRID_STRIDE(v, n) {
-    parent[v] = -1;
     const bool root = adeg[v] > 0 && root_of[label[v]] == (int32_t)v;
+    parent[v] = root ? -1 : INT32_MAX;  // the BFS takes the minimum over the level above
     level[v] = root ? 0 : -1;
     if (root) push_aggr(order, tail, (int32_t)v);
   }
@@ -108,134 +110,131 @@ __device__ __forceinline__ bool is_tree_edge(const int32_t *parent, int32_t u, i
   return parent[w] == u || parent[u] == w;
 }
 
-// ------------------------------------------------ grid barrier (bounded)
-// Sense-reversing barrier over all CTAs of a cooperative launch (which
-// guarantees they are co-resident).  Each wait polls at most `limit` times;
-// a CTA that runs out, or that sees another CTA's error, sets ERR_TIMEOUT
-// and the kernel returns, so no wait is unbounded.
-struct GridBarrier {
-  unsigned int *count;
-  unsigned int *gen;
-  int *err;
-  long long limit;
-};
+constexpr int FOREST_THREADS = 1024;
+constexpr int FOREST_SUB = 8;  // lanes per frontier row in the BFS
 
-__device__ bool grid_wait(const GridBarrier &b) {
-  __shared__ int s_ok;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int ok = 1;
-    const unsigned int g = *(volatile unsigned int *)b.gen;
-    __threadfence();
-    if (atomicAdd(b.count, 1u) == gridDim.x - 1) {
-      *(volatile unsigned int *)b.count = 0u;
-      __threadfence();
-      atomicAdd(b.gen, 1u);
-    } else {
-      long long polls = 0;
-      while (*(volatile unsigned int *)b.gen == g) {
-        if (polls++ >= b.limit || *(volatile int *)b.err) {
-          ok = 0;
-          break;
-        }
-      }
-    }
-    __threadfence();
-    if (!ok) atomicOr(b.err, ERR_TIMEOUT);
-    s_ok = ok;
+__device__ __forceinline__ void stamp(long long *stamps, int k) {
+  if (stamps && blockIdx.x == 0 && threadIdx.x == 0) {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    stamps[k] = t;
   }
-  __syncthreads();
-  return s_ok != 0;
 }
 
-constexpr int FOREST_THREADS = 1024;
+__device__ __forceinline__ int64_t vload64(const int64_t *p) { return *(volatile const int64_t *)p; }
 
-#define COOP_STRIDE(i, lo, hi) \
-  for (int64_t i = (lo) + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (hi); i += (int64_t)gridDim.x * blockDim.x)
-
-// The whole spanning-forest pass in one cooperative launch: BFS levels
-// (roots already queued), then subtree sizes and reach sums bottom-up,
-// preorder top-down, and low/high.  lvl_off[l] is where level l starts in
-// order[]; out[0] = number of levels, out[1] = forest size.
+// The whole spanning-forest pass in one cooperative launch.
+//  1. BFS levels from the queued roots (one grid-wide wait per level), a
+//     frontier vertex's row walked by FOREST_SUB lanes; the parent of w is
+//     its smallest-id neighbour on the level above (an atomic minimum over
+//     the edges that reach w), and each parent counts its children one
+//     level later, once the minimum is final.
+//  2. Subtree sizes nd, reach sums subR and sibling offsets off, bottom-up
+//     without level waits: every leaf starts a walk towards its root and a
+//     vertex is passed on by whichever child completes it last (the
+//     completion counter is bumped after a fence, so the last arriver sees
+//     every sibling's sums).  off[c] is c's place among its siblings, taken
+//     with one atomic on the parent's cursor once nd[c] is final.
+//  3. Preorder pre[v] = pre[parent] + 1 + off[v]: each vertex walks up until
+//     it meets an ancestor whose number is already published, so no vertex
+//     ever waits; subtrees are contiguous ranges [pre, pre + nd).
+//  4. low/high: own preorder number and those of non-tree neighbours, then
+//     min/max over subtrees with the same last-arriver walk as step 2.
+// out[0] = number of levels, out[1] = forest size.  `stamps` (optional)
+// receives the global timer at each phase boundary.
 __global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                               const uint8_t *__restrict__ alive, const int32_t *__restrict__ reach, int32_t *level,
-                              int32_t *parent, int32_t *order, unsigned long long *lcount, int32_t *lvl_off,
-                              int32_t *nd, int64_t *subR, int32_t *pre, int32_t *low, int32_t *high, int32_t *out,
-                              const unsigned long long *nroots, int32_t *cursor, GridBarrier bar) {
+                              int32_t *parent, int32_t *order, unsigned long long *lcount, int32_t *nchild,
+                              int32_t *done, int32_t *off, int32_t *nd, int64_t *subR, int32_t *pre, int32_t *low,
+                              int32_t *high, int32_t *out, const unsigned long long *nroots, int32_t *cursor,
+                              long long *stamps, GridBarrier bar) {
   // lcount[l] counts the vertices discovered on level l (one counter per
   // level, so reading one level's size never races with the next level's
   // discovery and a single barrier per level suffices)
   const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  stamp(stamps, 0);
   int64_t lo = 0, hi = (int64_t)*nroots;
   int L = 0;
-  if (lead) {
-    lvl_off[0] = 0;
-    lvl_off[1] = (int32_t)hi;
-  }
+  const int sl = (int)(threadIdx.x % FOREST_SUB);
+  const int64_t sub0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / FOREST_SUB;
+  const int64_t nsub = (int64_t)gridDim.x * blockDim.x / FOREST_SUB;
   for (;;) {
-    COOP_STRIDE(i, lo, hi) {  // discover level L+1
+    for (int64_t i = lo + sub0; i < hi; i += nsub) {  // discover level L+1
       const int32_t v = order[i];
-      for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
+      if (sl == 0 && L > 0) atomicAdd(nchild + uf_vload(parent + v), 1);  // final since the last wait
+      for (int64_t k = rp[v] + sl; k < rp[v + 1]; k += FOREST_SUB) {
         const int32_t w = col[k];
-        if (!alive[w] || uf_vload(level + w) >= 0) continue;
-        if (atomicCAS(level + w, -1, L + 1) == -1) {
-          const unsigned mask = __activemask();
-          const int leader = __ffs(mask) - 1;
-          const int ln = threadIdx.x & 31;
-          unsigned long long base = 0;
-          if (ln == leader) base = atomicAdd(lcount + L + 1, (unsigned long long)__popc(mask));
-          base = __shfl_sync(mask, base, leader);
-          order[hi + base + __popc(mask & ((1u << ln) - 1))] = w;
+        if (!alive[w]) continue;
+        int32_t lw = uf_vload(level + w);
+        if (lw < 0) {
+          lw = atomicCAS(level + w, -1, L + 1);
+          if (lw < 0) {
+            const unsigned mask = __activemask();
+            const int leader = __ffs(mask) - 1;
+            const int ln = threadIdx.x & 31;
+            unsigned long long base = 0;
+            if (ln == leader) base = atomicAdd(lcount + L + 1, (unsigned long long)__popc(mask));
+            base = __shfl_sync(mask, base, leader);
+            order[hi + base + __popc(mask & ((1u << ln) - 1))] = w;
+          }
         }
+        if (lw < 0 || lw == L + 1) atomicMin(parent + w, v);
       }
     }
     if (!grid_wait(bar)) return;
     const int64_t nhi = hi + (int64_t)*(volatile unsigned long long *)(lcount + L + 1);
     if (nhi == hi) break;
-    COOP_STRIDE(i, hi, nhi) {  // parent = smallest-id neighbour on level L
-      const int32_t w = order[i];
-      int32_t p = INT32_MAX;
-      for (int64_t k = rp[w]; k < rp[w + 1]; k++) {
-        const int32_t v = col[k];
-        if (alive[v] && level[v] == L && v < p) p = v;
-      }
-      parent[w] = p;
-    }
     lo = hi;
     hi = nhi;
     L++;
-    if (lead) lvl_off[L + 1] = (int32_t)hi;
   }
   const int nlev = L + 1;
   const int64_t cnt = hi;
+  stamp(stamps, 1);
   COOP_STRIDE(i, 0, cnt) {
     const int32_t v = order[i];
     nd[v] = 1;
     subR[v] = reach[v];
-    pre[v] = 0;
+    pre[v] = level[v] == 0 ? 0 : -1;
     cursor[v] = 0;
+    done[v] = 0;
   }
   if (!grid_wait(bar)) return;
-  for (int l = nlev - 1; l >= 1; l--) {  // subtree sizes and reach sums
-    COOP_STRIDE(i, lvl_off[l], lvl_off[l + 1]) {
-      const int32_t v = order[i];
+  COOP_STRIDE(i, 0, cnt) {  // subtree sizes, reach sums and sibling offsets
+    int32_t v = order[i];
+    if (nchild[v] != 0) continue;
+    while (level[v] != 0) {
       const int32_t p = parent[v];
-      atomicAdd(nd + p, nd[v]);
-      atomicAdd((unsigned long long *)(subR + p), (unsigned long long)subR[v]);
+      const int32_t ndv = uf_vload(nd + v);
+      off[v] = atomicAdd(cursor + p, ndv);
+      atomicAdd(nd + p, ndv);
+      atomicAdd((unsigned long long *)(subR + p), (unsigned long long)vload64(subR + v));
+      __threadfence();
+      if (atomicAdd(done + p, 1) + 1 != nchild[p]) break;
+      __threadfence();
+      v = p;
     }
-    if (!grid_wait(bar)) return;
   }
-  // preorder, level by level: each child takes the next free range of its
-  // parent with one atomic (any order of siblings gives contiguous subtree
-  // ranges; the blocks do not depend on it)
-  for (int l = 1; l < nlev; l++) {
-    COOP_STRIDE(i, lvl_off[l], lvl_off[l + 1]) {
-      const int32_t c = order[i];
-      const int32_t p = parent[c];
-      pre[c] = pre[p] + 1 + atomicAdd(cursor + p, nd[c]);
+  if (!grid_wait(bar)) return;
+  stamp(stamps, 2);
+  COOP_STRIDE(i, 0, cnt) {  // preorder numbers
+    const int32_t v = order[i];
+    if (level[v] == 0) continue;
+    int32_t acc = 0, a = v;
+    for (;;) {
+      acc += 1 + off[a];
+      const int32_t p = parent[a];
+      const int32_t pp = uf_vload(pre + p);
+      if (pp >= 0) {
+        acc += pp;
+        break;
+      }
+      a = p;
     }
-    if (!grid_wait(bar)) return;
+    *(volatile int32_t *)(pre + v) = acc;
   }
+  if (!grid_wait(bar)) return;
+  stamp(stamps, 3);
   COOP_STRIDE(i, 0, cnt) {  // own pre and the far ends of non-tree edges
     const int32_t u = order[i];
     int32_t a = pre[u], b = pre[u];
@@ -247,17 +246,24 @@ __global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__r
     }
     low[u] = a;
     high[u] = b;
+    done[u] = 0;
   }
   if (!grid_wait(bar)) return;
-  for (int l = nlev - 1; l >= 1; l--) {  // low/high over subtrees
-    COOP_STRIDE(i, lvl_off[l], lvl_off[l + 1]) {
-      const int32_t v = order[i];
+  COOP_STRIDE(i, 0, cnt) {  // low/high over subtrees
+    int32_t v = order[i];
+    if (nchild[v] != 0) continue;
+    while (level[v] != 0) {
       const int32_t p = parent[v];
-      atomicMin(low + p, low[v]);
-      atomicMax(high + p, high[v]);
+      atomicMin(low + p, uf_vload(low + v));
+      atomicMax(high + p, uf_vload(high + v));
+      __threadfence();
+      if (atomicAdd(done + p, 1) + 1 != nchild[p]) break;
+      __threadfence();
+      v = p;
     }
-    if (!grid_wait(bar)) return;
   }
+  if (!grid_wait(bar)) return;
+  stamp(stamps, 4);
   if (lead) {
     out[0] = nlev;
     out[1] = (int32_t)cnt;
@@ -485,10 +491,14 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     BCS_TRY(high.alloc(n, ctx.stream));
     BCS_TRY(uf.alloc(n, ctx.stream));
     BCS_TRY(blk.alloc(n, ctx.stream));
-    DBuf<int32_t> lvl_off_d, fout, ferr;
+    DBuf<int32_t> nchild, done, off, fout, ferr;
     DBuf<unsigned int> barw;
     DBuf<unsigned long long> lcount;
-    BCS_TRY(lvl_off_d.alloc(n + 2, ctx.stream));
+    DBuf<long long> stamps;
+    BCS_TRY(nchild.alloc(n, ctx.stream));
+    BCS_TRY(done.alloc(n, ctx.stream));
+    BCS_TRY(off.alloc(n, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(nchild.p, 0, n * sizeof(int32_t), ctx.stream));
     BCS_TRY(lcount.alloc(n + 2, ctx.stream));
     BCS_CUDA(cudaMemsetAsync(lcount.p, 0, (n + 2) * sizeof(unsigned long long), ctx.stream));
     BCS_TRY(fout.alloc(2, ctx.stream));
@@ -497,6 +507,10 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     BCS_CUDA(cudaMemsetAsync(barw.p, 0, 2 * sizeof(unsigned int), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(ferr.p, 0, sizeof(int32_t), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(fout.p, 0, 2 * sizeof(int32_t), ctx.stream));
+    if (tr.on) {
+      BCS_TRY(stamps.alloc(5, ctx.stream));
+      BCS_CUDA(cudaMemsetAsync(stamps.p, 0, 5 * sizeof(long long), ctx.stream));
+    }
     // one CTA of FOREST_THREADS per SM: few arrivals per grid-wide wait
     int per_sm = 0;
     BCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_forest_coop, FOREST_THREADS, 0));
@@ -510,18 +524,20 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     const unsigned long long *nrootsp = (const unsigned long long *)tot.p;
     DBuf<int32_t> cursor;
     BCS_TRY(cursor.alloc(n, ctx.stream));
-    int32_t *cursorp = cursor.p;
-    int32_t *lvlp = lvl_off_d.p, *ndp = nd.p, *prep = pre.p, *lowp = low.p, *highp = high.p, *foutp = fout.p;
+    int32_t *cursorp = cursor.p, *nchildp = nchild.p, *donep = done.p, *offp = off.p;
+    int32_t *ndp = nd.p, *prep = pre.p, *lowp = low.p, *highp = high.p, *foutp = fout.p;
     int64_t *subRp = subR.p;
     int32_t *levelp = level.p, *parentp = parent.p, *orderp = order.p;
+    long long *stampsp = stamps.p;
     const int64_t *rpp = g.rp;
     const int32_t *colp = g.col;
     const uint8_t *alivep = alive;
     const int32_t *reachp = reach;
-    void *args[] = {(void *)&rpp,   (void *)&colp,  (void *)&alivep, (void *)&reachp, (void *)&levelp,
-                    (void *)&parentp, (void *)&orderp, (void *)&lcountp, (void *)&lvlp,   (void *)&ndp,
-                    (void *)&subRp, (void *)&prep,  (void *)&lowp,   (void *)&highp,  (void *)&foutp,
-                    (void *)&nrootsp, (void *)&cursorp, (void *)&gb};
+    void *args[] = {(void *)&rpp,     (void *)&colp,   (void *)&alivep, (void *)&reachp,  (void *)&levelp,
+                    (void *)&parentp, (void *)&orderp, (void *)&lcountp, (void *)&nchildp, (void *)&donep,
+                    (void *)&offp,    (void *)&ndp,    (void *)&subRp,  (void *)&prep,    (void *)&lowp,
+                    (void *)&highp,   (void *)&foutp,  (void *)&nrootsp, (void *)&cursorp, (void *)&stampsp,
+                    (void *)&gb};
     BCS_CUDA(cudaLaunchCooperativeKernel((const void *)k_forest_coop, dim3(coop_grid), dim3(FOREST_THREADS), args, 0,
                                          ctx.stream));
     ctx.launches++;
@@ -532,6 +548,12 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     if (hres[2] & ERR_TIMEOUT) {
       set_error("a grid-wide wait of the spanning-forest kernel ran out (opts->max_wait)");
       return BCS_ETIMEOUT;
+    }
+    if (tr.on) {
+      long long ts[5];
+      BCS_CUDA(cudaMemcpy(ts, stamps.p, sizeof(ts), cudaMemcpyDeviceToHost));
+      std::fprintf(stderr, "[bcs trace] forest phases: bfs %.3f sizes %.3f preorder %.3f lowhigh %.3f ms\n",
+                   (ts[1] - ts[0]) * 1e-6, (ts[2] - ts[1]) * 1e-6, (ts[3] - ts[2]) * 1e-6, (ts[4] - ts[3]) * 1e-6);
     }
     const int nlev_h = hres[0];
     tree_cnt = hres[1];

@@ -4,6 +4,7 @@
 #include <mutex>
 
 #include "common.h"
+#include "coop.cuh"
 #include "uf.cuh"
 
 namespace bcs {
@@ -16,26 +17,6 @@ static inline int grid_for(int64_t work, int block, int max_blocks) {
 }
 
 // Pinned 8-byte scratch per host thread for small device->host reads.
-static int64_t *pinned_scalar() {
-  static thread_local int64_t *p = nullptr;
-  if (!p) {
-    if (cudaMallocHost((void **)&p, 4 * sizeof(int64_t)) != cudaSuccess) p = nullptr;
-  }
-  return p;
-}
-
-static int read_scalar(Ctx &ctx, const int64_t *d_src, int64_t *out) {
-  int64_t *h = pinned_scalar();
-  if (!h) {
-    set_error("cudaMallocHost of a pinned scalar failed");
-    return BCS_ENOMEM;
-  }
-  BCS_CUDA(cudaMemcpyAsync(h, d_src, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
-  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
-  *out = *h;
-  return BCS_OK;
-}
-
 // ---------------------------------------------------------------- validate
 // Warp per row: bounds, self-loops, strictly ascending rows (no duplicates)
 // and symmetry (binary search of u in the row of each neighbour).
@@ -162,19 +143,35 @@ __global__ void k_cc_sample(int64_t n, const int32_t *__restrict__ parent, int32
   if (t == 0) *dominant = (int32_t)(best & 0xffffffffull);
 }
 
+// One vertex per thread; the remaining edges of a vertex with more than 32
+// of them are walked by its whole warp instead.
 __global__ void k_cc_link_rest(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                                int32_t *parent, const int32_t *__restrict__ dominant) {
   const int lane = threadIdx.x & 31;
-  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int32_t c = *dominant;
-  for (int64_t u = warp; u < n; u += nwarps) {
-    if (uf_find(parent, (int32_t)u) == c) continue;  // warp-uniform: every lane has the same u
-    const int64_t b = rp[u] + CC_FIRST, e = rp[u + 1];
-    for (int64_t k = b + lane; k < e; k += 32) {
-      const int32_t v = col[k];
-      // after the compression most linked pairs already share a parent
-      if (uf_vload(parent + u) != uf_vload(parent + v)) uf_unite(parent, (int32_t)u, v);
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
+    const int64_t u = base + lane;  // warp-uniform trip count: `base` is the same across the warp
+    int64_t b = 0, e = 0;
+    if (u < n && uf_find(parent, (int32_t)u) != c) {
+      b = rp[u] + CC_FIRST;
+      e = rp[u + 1];
+    }
+    const bool wide = e - b > 32;
+    if (!wide)
+      for (int64_t k = b; k < e; k++) {
+        const int32_t v = col[k];
+        // after the compression most linked pairs already share a parent
+        if (uf_vload(parent + u) != uf_vload(parent + v)) uf_unite(parent, (int32_t)u, v);
+      }
+    for (unsigned m = __ballot_sync(0xffffffffu, wide); m; m &= m - 1) {
+      const int src = __ffs(m) - 1;
+      const int64_t wu = __shfl_sync(0xffffffffu, u, src);
+      const int64_t wb = __shfl_sync(0xffffffffu, b, src), we = __shfl_sync(0xffffffffu, e, src);
+      for (int64_t k = wb + lane; k < we; k += 32) {
+        const int32_t v = col[k];
+        if (uf_vload(parent + wu) != uf_vload(parent + v)) uf_unite(parent, (int32_t)wu, v);
+      }
     }
   }
 }
@@ -213,8 +210,7 @@ int launch_cc(Ctx &ctx, const DevGraph &g, int32_t *d_label, int64_t *d_N) {
   k_cc_link_first<<<gv, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p);
   k_cc_compress<<<gv, block, 0, ctx.stream>>>(g.n, parent.p);
   k_cc_sample<<<1, CC_SAMPLE, 0, ctx.stream>>>(g.n, parent.p, dom.p);
-  int gw = grid_for(g.n * 32, block, ctx.num_sms * 16);
-  k_cc_link_rest<<<gw, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p, dom.p);
+  k_cc_link_rest<<<gv, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p, dom.p);
   k_cc_finish<<<gv, block, 0, ctx.stream>>>(g.n, parent.p, d_label, (unsigned long long *)cnt.p);
   k_cc_size<<<gv, block, 0, ctx.stream>>>(g.n, d_label, cnt.p, d_N);
   ctx.launches += 7;
@@ -242,94 +238,118 @@ __device__ __forceinline__ void push_warp_aggregated(int32_t *queue, unsigned lo
   queue[base + rank] = v;
 }
 
-__global__ void k_peel_init(int64_t n, const int64_t *__restrict__ rp, int32_t *deg, int32_t *reach,
-                            uint8_t *alive, int64_t *bcpre, int32_t *frontier, unsigned long long *fcount) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-    int32_t d = (int32_t)(rp[v + 1] - rp[v]);
+constexpr int PEEL_THREADS = 1024;
+
+// All rounds in one cooperative launch.  cnt[r] is the size of round r's
+// frontier (one counter per round, so no counter is reset while another CTA
+// may still read it); a round decides every removal against the degrees at
+// its start, waits, then applies them.  The arrays the rounds change (deg,
+// reach, alive, bcpre) are plain pointers: no read of them may go through
+// the non-coherent read-only path.  out[0] = rounds run.
+__global__ void k_peel_coop(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
+                            const int64_t *__restrict__ N, int32_t *deg, int32_t *reach, uint8_t *alive,
+                            int64_t *bcpre, int32_t *fa, int32_t *fb, int32_t *target, unsigned long long *cnt,
+                            int64_t *out, GridBarrier bar) {
+  COOP_STRIDE(v, 0, n) {
+    const int32_t d = (int32_t)(rp[v + 1] - rp[v]);
     deg[v] = d;
     reach[v] = 1;
     alive[v] = 1;
     bcpre[v] = 0;
-    if (d == 1) push_warp_aggregated(frontier, fcount, (int32_t)v);
+    if (d == 1) push_warp_aggregated(fa, cnt, (int32_t)v);
   }
-}
-
-// target[i] = the neighbour the i-th frontier vertex is removed into, or -1
-__global__ void k_peel_decide(int64_t fcount, const int32_t *__restrict__ frontier, const int64_t *__restrict__ rp,
-                              const int32_t *__restrict__ col, const int32_t *__restrict__ deg,
-                              const uint8_t *__restrict__ alive, int32_t *target) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t u = frontier[i];
-    int32_t t = -1;
-    if (alive[u] && deg[u] == 1) {
-      int32_t v = -1;
-      for (int64_t k = rp[u]; k < rp[u + 1]; k++) {
-        if (alive[col[k]]) {
-          v = col[k];
-          break;
+  if (!grid_wait(bar)) return;
+  int32_t *cur = fa, *nxt = fb;
+  int64_t r = 0;
+  for (;; r++) {
+    const int64_t fcount = (int64_t)*(volatile unsigned long long *)(cnt + r);
+    if (fcount == 0) break;
+    COOP_STRIDE(i, 0, fcount) {  // target = the neighbour u is removed into, or -1
+      const int32_t u = cur[i];
+      int32_t t = -1;
+      if (alive[u] && deg[u] == 1) {
+        int32_t v = -1;
+        for (int64_t k = rp[u]; k < rp[u + 1]; k++) {
+          if (alive[col[k]]) {
+            v = col[k];
+            break;
+          }
         }
+        if (v >= 0 && !(deg[v] == 1 && u < v)) t = v;
       }
-      if (v >= 0 && !(deg[v] == 1 && u < v)) t = v;
+      target[i] = t;
     }
-    target[i] = t;
+    if (!grid_wait(bar)) return;
+    COOP_STRIDE(i, 0, fcount) {
+      const int32_t v = target[i];
+      if (v < 0) continue;
+      const int32_t u = cur[i];
+      const int64_t ru = reach[u];
+      const int64_t nc = N[u];
+      atomicAdd((unsigned long long *)(bcpre + u), (unsigned long long)((ru - 1) * (nc - ru)));
+      atomicAdd((unsigned long long *)(bcpre + v), (unsigned long long)(ru * (nc - ru - 1)));
+      atomicAdd(reach + v, (int32_t)ru);
+      alive[u] = 0;
+      deg[u] = 0;
+      if (atomicSub(deg + v, 1) == 2) push_warp_aggregated(nxt, cnt + r + 1, v);
+    }
+    if (!grid_wait(bar)) return;
+    int32_t *t = cur;
+    cur = nxt;
+    nxt = t;
   }
-}
-
-__global__ void k_peel_apply(int64_t fcount, const int32_t *__restrict__ frontier, const int32_t *__restrict__ target,
-                             const int64_t *__restrict__ N, int32_t *deg, int32_t *reach, uint8_t *alive,
-                             int64_t *bcpre, int32_t *next, unsigned long long *ncount) {
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < fcount; i += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t v = target[i];
-    if (v < 0) continue;
-    const int32_t u = frontier[i];
-    const int64_t r = reach[u];
-    const int64_t nc = N[u];
-    atomicAdd((unsigned long long *)(bcpre + u), (unsigned long long)((r - 1) * (nc - r)));
-    atomicAdd((unsigned long long *)(bcpre + v), (unsigned long long)(r * (nc - r - 1)));
-    atomicAdd(reach + v, (int32_t)r);
-    alive[u] = 0;
-    deg[u] = 0;
-    if (atomicSub(deg + v, 1) == 2) push_warp_aggregated(next, ncount, v);
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) out[0] = r;
 }
 
 int run_peel(Ctx &ctx, const DevGraph &g, const int64_t *d_N, uint8_t *d_alive, int32_t *d_reach,
              int64_t *d_bcpre) {
   if (g.n == 0) return BCS_OK;
-  DBuf<int32_t> deg, fa, fb, target;
-  DBuf<int64_t> counts;
+  DBuf<int32_t> deg, fa, fb, target, err;
+  DBuf<unsigned long long> cnt;
+  DBuf<unsigned int> barw;
+  DBuf<int64_t> out;
   BCS_TRY(deg.alloc(g.n, ctx.stream));
   BCS_TRY(fa.alloc(g.n, ctx.stream));
   BCS_TRY(fb.alloc(g.n, ctx.stream));
   BCS_TRY(target.alloc(g.n, ctx.stream));
-  BCS_TRY(counts.alloc(2, ctx.stream));
-  BCS_CUDA(cudaMemsetAsync(counts.p, 0, 2 * sizeof(int64_t), ctx.stream));
-  int block = 256;
-  int gv = grid_for(g.n, block, ctx.num_sms * 32);
-  k_peel_init<<<gv, block, 0, ctx.stream>>>(g.n, g.rp, deg.p, d_reach, d_alive, d_bcpre, fa.p,
-                                            (unsigned long long *)counts.p);
-  ctx.launches++;
-  BCS_CUDA(cudaGetLastError());
-  int64_t fcount = 0;
-  BCS_TRY(read_scalar(ctx, counts.p, &fcount));
-  int32_t *cur = fa.p, *nxt = fb.p;
-  int cur_slot = 0;
-  int64_t rounds = 0;
-  while (fcount > 0) {
-    int nxt_slot = 1 - cur_slot;
-    BCS_CUDA(cudaMemsetAsync(counts.p + nxt_slot, 0, sizeof(int64_t), ctx.stream));
-    int gf = grid_for(fcount, block, ctx.num_sms * 32);
-    k_peel_decide<<<gf, block, 0, ctx.stream>>>(fcount, cur, g.rp, g.col, deg.p, d_alive, target.p);
-    k_peel_apply<<<gf, block, 0, ctx.stream>>>(fcount, cur, target.p, d_N, deg.p, d_reach, d_alive, d_bcpre, nxt,
-                                               (unsigned long long *)(counts.p + nxt_slot));
-    ctx.launches += 2;
-    BCS_CUDA(cudaGetLastError());
-    BCS_TRY(read_scalar(ctx, counts.p + nxt_slot, &fcount));
-    std::swap(cur, nxt);
-    cur_slot = nxt_slot;
-    rounds++;
+  BCS_TRY(cnt.alloc(g.n + 2, ctx.stream));  // a round removes at least one vertex: at most n rounds
+  BCS_TRY(barw.alloc(2, ctx.stream));
+  BCS_TRY(err.alloc(1, ctx.stream));
+  BCS_TRY(out.alloc(1, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(cnt.p, 0, (g.n + 2) * sizeof(unsigned long long), ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(barw.p, 0, 2 * sizeof(unsigned int), ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int32_t), ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(out.p, 0, sizeof(int64_t), ctx.stream));
+  int per_sm = 0;
+  BCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel_coop, PEEL_THREADS, 0));
+  if (per_sm < 1) {
+    set_error("the degree-1 removal kernel cannot be resident");
+    return BCS_ECUDA;
   }
-  ctx.stats.peel_rounds = rounds;
+  GridBarrier gb{barw.p, barw.p + 1, err.p, (long long)ctx.max_wait};
+  int64_t n = g.n;
+  const int64_t *rpp = g.rp, *Np = d_N;
+  const int32_t *colp = g.col;
+  int32_t *degp = deg.p, *reachp = d_reach, *fap = fa.p, *fbp = fb.p, *tp = target.p;
+  uint8_t *alivep = d_alive;
+  int64_t *bcp = d_bcpre, *outp = out.p;
+  unsigned long long *cntp = cnt.p;
+  void *args[] = {(void *)&n,     (void *)&rpp,   (void *)&colp, (void *)&Np,   (void *)&degp,
+                  (void *)&reachp, (void *)&alivep, (void *)&bcp,  (void *)&fap,  (void *)&fbp,
+                  (void *)&tp,    (void *)&cntp,  (void *)&outp, (void *)&gb};
+  BCS_CUDA(cudaLaunchCooperativeKernel((const void *)k_peel_coop, dim3(ctx.num_sms), dim3(PEEL_THREADS), args, 0,
+                                       ctx.stream));
+  ctx.launches++;
+  int64_t res[2] = {0, 0};
+  BCS_CUDA(cudaMemcpyAsync(res, out.p, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
+  int32_t e = 0;
+  BCS_CUDA(cudaMemcpyAsync(&e, err.p, sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  if (e & ERR_TIMEOUT) {
+    set_error("a grid-wide wait of the degree-1 removal kernel ran out (opts->max_wait)");
+    return BCS_ETIMEOUT;
+  }
+  ctx.stats.peel_rounds = res[0];
   return BCS_OK;
 }
 
