@@ -128,14 +128,23 @@ def workload(scale: int):
                "n": g.n, "m": g.m, "seed": g.meta["seed"], "delta": "fp64"}
 
 
+KERNEL_SOURCES = ("bcreach.cu", "bc_math.cuh")  # what the Bc-Reach kernels compile from
+
+
+def kernel_source_sha1() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        h.update(open(os.path.join(ROOT, "paper_1209_6007_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()
+
+
 def measured_traffic():
     """DRAM bytes per launch of the Bc-Reach kernel from the committed ncu
-    summary, if it was taken on the current kernel source (else None)."""
-    import hashlib
+    summary, if it was taken on the current kernel sources (else None)."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "bcreach_small_articulation.json")))
-        src = open(os.path.join(ROOT, "paper_1209_6007_gb300", "csrc", "bcreach.cu"), "rb").read()
-        if rec.get("source_sha1") == hashlib.sha1(src).hexdigest():
+        if rec.get("source_sha1") == kernel_source_sha1():
             return float(rec["dram_bytes_per_launch"])
     except (OSError, ValueError, KeyError):
         pass
