@@ -93,7 +93,7 @@ template <bool FP32>
 struct SrcState {
   int32_t *d;
   double *sig;
-  typename CoefT<FP32>::type *coef;  // phase 1 keeps sigma * ident here
+  typename CoefT<FP32>::type *coef;  // global path: sigma * ident in phase 1; shared path: == sig
   int32_t *queue;
   uint32_t *dmask;     // shared-memory path: DAG successors among the first 32 row entries
   int32_t *lvl_start;  // levels + 2
@@ -153,9 +153,13 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   int32_t *const d = st.d;
   double *const sig = st.sig;
   long long *const sigi = (long long *)st.sig;
-  double *const sk = (double *)st.coef;  // sigma[v] * (v == s ? 1 : ident[v]) during phase 1
+  double *const sk = (double *)st.coef;  // global path: sigma[v] * (v == s ? 1 : ident[v]) in phase 1
   long long *const ski = (long long *)st.coef;
   constexpr bool PUSH = !RESET_BY_QUEUE;
+  // Shared-memory path: the coefficient of phase 2 overwrites the path count
+  // of the same vertex (st.coef == st.sig); phase 1 keeps sigma alone and
+  // multiplies by ident where it reads it.
+  constexpr bool ALIAS = PUSH;
   long long *const pull_src = IDENT ? ski : sigi;  // sigma * ident (the source counts once)
   if (!RESET_BY_QUEUE) {
     for (int v = g.rank; v < n; v += g.size) {
@@ -222,11 +226,14 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
     if (nhi == hi) break;
     blg += flg;
     if (lint > L + 1 && blg >= 62) {
-      // level L+1 may not fit 63 bits: level L becomes FP64 once
-      lint = L + 1;
+      // level L+1 may not fit 63 bits: it is pulled in FP64 from level L
+      // (shared-memory path: level L's counts turn FP64 in place, so level L
+      // is the first FP64 level)
+      lint = ALIAS ? L : L + 1;
       for (int i = lo + g.rank; i < hi; i += g.size) {
         const int32_t v = st.queue[i];
-        sk[v] = PUSH ? (double)sigi[v] * (IDENT && v != s ? (double)wt.ident[v] : 1.0) : (double)pull_src[v];
+        if (ALIAS) sig[v] = (double)sigi[v];
+        else sk[v] = (double)pull_src[v];
       }
       g.sync();
     }
@@ -251,10 +258,10 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
         const RowT eb = row[w], ee = row[w + 1];
         for (RowT e = eb; e < ee; e++) {
           const int32_t u = (int32_t)col[e];
-          if (d[u] == L) a += sk[u];
+          if (d[u] == L) a += ALIAS ? (IDENT && u != s ? sig[u] * wt.ident_d[u] : sig[u]) : sk[u];
         }
         sig[w] = a;
-        sk[w] = IDENT ? a * (wt.ident_d ? wt.ident_d[w] : (double)wt.ident[w]) : a;
+        if (!ALIAS) sk[w] = IDENT ? a * (wt.ident_d ? wt.ident_d[w] : (double)wt.ident[w]) : a;
       }
       if (blg > 900) {
         g.sync();
@@ -268,7 +275,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
           for (int i = hi + g.rank; i < nhi; i += g.size) {
             const int32_t w = st.queue[i];
             sig[w] = scalbn(sig[w], -k);
-            sk[w] = scalbn(sk[w], -k);
+            if (!ALIAS) sk[w] = scalbn(sk[w], -k);
           }
           m = scalbn(m, -k);
           ecur += k;
@@ -395,10 +402,10 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
 // ---------------------------------------------------------- small path
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// per group: distances, queue and DAG masks (4 bytes each), path counts,
-// coefficients and the group's bc accumulator (8 bytes each)
+// per group: distances, queue and DAG masks (4 bytes each), path counts
+// (later the coefficients, in place) and the group's bc accumulator (8 bytes each)
 __host__ __device__ inline size_t small_group_bytes(int64_t n) {
-  return align16((size_t)n * 4) * 3 + align16((size_t)n * 8) * 3;
+  return align16((size_t)n * 4) * 3 + align16((size_t)n * 8) * 2;
 }
 
 // bytes of shared memory a component needs with `ng` concurrent sources:
@@ -470,7 +477,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     // zero every group's accumulator
     for (int x = tid; x < ng * n; x += SMALL_THREADS) {
       const int gi = x / n, v = x - gi * n;
-      double *a = (double *)(p + per * gi + align16((size_t)n * 4) * 3 + align16((size_t)n * 8) * 2);
+      double *a = (double *)(p + per * gi + align16((size_t)n * 4) * 3 + align16((size_t)n * 8));
       a[v] = 0.0;
     }
     __syncthreads();
@@ -486,8 +493,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.dmask = (uint32_t *)q;
     q += align16((size_t)n * 4);
     st.sig = (double *)q;
-    q += align16((size_t)n * 8);
-    st.coef = (typename CoefT<FP32>::type *)q;
+    st.coef = (typename CoefT<FP32>::type *)q;  // same storage (see bcreach_source)
     q += align16((size_t)n * 8);
     double *acc = (double *)q;
     int32_t *lv = lvl_scratch + ((size_t)blockIdx.x * SMALL_MAX_GROUPS + gid) * (size_t)lvl_stride * 2;
@@ -505,7 +511,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     for (int v = tid; v < n; v += SMALL_THREADS) {
       double t = 0.0;
       for (int gi = 0; gi < ng; gi++)
-        t += ((const double *)(p + per * gi + align16((size_t)n * 4) * 3 + align16((size_t)n * 8) * 2))[v];
+        t += ((const double *)(p + per * gi + align16((size_t)n * 4) * 3 + align16((size_t)n * 8)))[v];
       if (t != 0.0) atomicAdd(bcp + c.vtx_off + v, t);
     }
     __syncthreads();
