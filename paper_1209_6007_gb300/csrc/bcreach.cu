@@ -45,6 +45,7 @@ constexpr int SMALL_THREADS = 256;
 // source does not fit goes to the global-memory path.
 constexpr size_t SMALL_SMEM = 100 * 1024;
 constexpr int SMALL_MAX_GROUPS = 8;
+constexpr int DISC_CH = 4;  // row entries per step of the shared-memory discovery pass (divides 32)
 constexpr int LARGE_THREADS = 512;
 
 struct SmallItem {
@@ -199,18 +200,36 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
         // sigma[v] * ident[v], formed by v's own lane (sigma[v] is final)
         const long long pv = !push ? 0 : (IDENT && v != s ? sigi[v] * (long long)wt.ident[v] : sigi[v]);
         uint32_t m = 0u;
-        for (RowT e = eb; e < ee; e++) {
-          const int32_t w = (int32_t)col[e];
-          int dw = vld(d + w);
-          if (dw < 0) {
-            dw = atomicCAS(d + w, -1, L + 1);
-            if (dw < 0) st.queue[atomicAdd(st.qtail, 1)] = w;
+        // DISC_CH row entries at a time, so that their shared-memory round
+        // trips overlap instead of forming one chain per entry
+        for (RowT e0 = eb; e0 < ee; e0 += DISC_CH) {
+          int32_t w[DISC_CH];
+          int dw[DISC_CH];
+#pragma unroll
+          for (int j = 0; j < DISC_CH; j++) w[j] = e0 + j < ee ? (int32_t)col[e0 + j] : -1;
+#pragma unroll
+          for (int j = 0; j < DISC_CH; j++) dw[j] = w[j] >= 0 ? vld(d + w[j]) : L;  // L: no DAG edge
+          unsigned won = 0u, dagb = 0u;
+#pragma unroll
+          for (int j = 0; j < DISC_CH; j++) {
+            const int r = dw[j] < 0 ? atomicCAS(d + w[j], -1, L + 1) : dw[j];
+            won |= (unsigned)(r < 0) << j;
+            dagb |= (unsigned)(r < 0 || r == L + 1) << j;
           }
-          if (dw < 0 || dw == L + 1) {
-            if (push32) atomicAdd((unsigned int *)(sigi + w), (unsigned int)pv);
-            else if (push) atomicAdd((unsigned long long *)(sigi + w), (unsigned long long)pv);
-            if (e - eb < 32) m |= 1u << (int)(e - eb);
+          if (won) {  // one counter update for the vertices this lane claimed
+            int pos = atomicAdd(st.qtail, __popc(won));
+#pragma unroll
+            for (int j = 0; j < DISC_CH; j++)
+              if (won >> j & 1u) st.queue[pos++] = w[j];
           }
+#pragma unroll
+          for (int j = 0; j < DISC_CH; j++) {
+            if (dagb >> j & 1u) {
+              if (push32) atomicAdd((unsigned int *)(sigi + w[j]), (unsigned int)pv);
+              else if (push) atomicAdd((unsigned long long *)(sigi + w[j]), (unsigned long long)pv);
+            }
+          }
+          if (e0 - eb < 32) m |= dagb << (int)(e0 - eb);
         }
         st.dmask[v] = m;
       } else {
@@ -326,7 +345,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
               for (int j = 0; j < cnt; j++) mask |= (uint32_t)(d[(int32_t)col[e0 + j]] == l + 1) << j;
             }
             ndag += __popc(mask);
-            while (mask) {
+            while (mask) {  // one FP64 add per successor (pairing them measured slower)
               const int j = __ffs(mask) - 1;
               mask &= mask - 1u;
               sum += ((const double *)st.coef)[(int32_t)col[e0 + j]];
@@ -358,12 +377,16 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
               for (int j = 0; j < cnt; j++) mask |= (uint32_t)(d[(int32_t)col[e0 + j]] == l + 1) << j;
             }
             ndag += __popc(mask);
-            while (mask) {
-              const int j = __ffs(mask) - 1;
+            while (mask) {  // two successors per step: their loads overlap
+              const int j0 = __ffs(mask) - 1;
               mask &= mask - 1u;
-              const Coef32 cw = ((const Coef32 *)st.coef)[(int32_t)col[e0 + j]];
-              const int x = ev - cw.e;  // <= 0: sigma[v] <= sigma[w]
-              if (x >= -126) sum = fmaf(cw.c, __int_as_float((127 + x) << 23), sum);
+              const int j1 = mask ? __ffs(mask) - 1 : -1;
+              mask &= mask - 1u;
+              const Coef32 c0 = ((const Coef32 *)st.coef)[(int32_t)col[e0 + j0]];
+              const Coef32 c1 = j1 >= 0 ? ((const Coef32 *)st.coef)[(int32_t)col[e0 + j1]] : Coef32{0.0f, ev};
+              const int x0 = ev - c0.e, x1 = ev - c1.e;  // <= 0: sigma[v] <= sigma[w]
+              if (x0 >= -126) sum = fmaf(c0.c, __int_as_float((127 + x0) << 23), sum);
+              if (x1 >= -126) sum = fmaf(c1.c, __int_as_float((127 + x1) << 23), sum);
             }
           }
         }
