@@ -36,6 +36,11 @@ double StageTimer::stop_ms() {
   return (double)ms;
 }
 
+static double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
 Tracer::Tracer(const char *scope_name, cudaStream_t stream)
     : scope(scope_name), s(stream), on(std::getenv("BCS_TRACE") != nullptr) {
   mark("start");
@@ -47,6 +52,7 @@ void Tracer::mark(const char *name) {
   if (cudaEventCreate(&e) != cudaSuccess) return;
   cudaEventRecord(e, s);
   marks.emplace_back(name, e);
+  host_ms.push_back(now_ms());
 }
 
 Tracer::~Tracer() {
@@ -56,11 +62,11 @@ Tracer::~Tracer() {
   for (size_t i = 1; i < marks.size(); i++) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, marks[i - 1].second, marks[i].second);
-    char buf[96];
-    std::snprintf(buf, sizeof(buf), " %s %.3f", marks[i].first, ms);
+    char buf[128];
+    std::snprintf(buf, sizeof(buf), " %s %.3f/%.3f", marks[i].first, ms, host_ms[i] - host_ms[i - 1]);
     line += buf;
   }
-  std::fprintf(stderr, "%s ms\n", line.c_str());
+  std::fprintf(stderr, "%s ms (gpu/host)\n", line.c_str());
   for (auto &m : marks) cudaEventDestroy(m.second);
 }
 
@@ -121,10 +127,6 @@ struct DeviceGuard {
   }
 };
 
-static double now_ms() {
-  using namespace std::chrono;
-  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
-}
 
 // ------------------------------------------------------------ input
 static int check_csr(const bcs_csr *g) {
@@ -284,6 +286,7 @@ static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t st
   BCS_TRY(reach.alloc(n, ctx.stream));
   BCS_TRY(alive.alloc(n, ctx.stream));
   BCS_TRY(S->bcpre.alloc(n, ctx.stream));
+  Tracer tr("shatter", ctx.stream);
   {
     StageTimer tm(ctx.stream);
     tm.start();
@@ -302,18 +305,21 @@ static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t st
     }
     ctx.stats.ms_peel = tm.stop_ms();
   }
+  tr.mark("cc+peel");
   {
     StageTimer tm(ctx.stream);
     tm.start();
     BCS_TRY(device_pieces(ctx, in.g, alive.p, reach.p, N.p, label.p, A, &S->pc));
     ctx.stats.ms_blocks = tm.stop_ms();
   }
+  tr.mark("pieces");
   {
     StageTimer tm(ctx.stream);
     tm.start();
     BCS_TRY(device_merge(ctx, S->pc, I, &S->merged));
     ctx.stats.ms_ident = tm.stop_ms();
   }
+  tr.mark("merge");
   // component descriptors
   const DevMerged &m = S->merged;
   const int64_t P = m.npieces;
@@ -341,11 +347,14 @@ static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t st
 
 static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double *bc_out,
                           const int64_t *batch_off = nullptr, int64_t batch_count = 0) {
+  Tracer tr("shattered", ctx.stream);
   Input in;
   BCS_TRY(upload_and_validate(ctx, h, &in, batch_off, batch_count));
+  tr.mark("validate");
   const uint32_t steps = o ? o->steps : BCS_STEPS_ALL;
   Shattered S;
   BCS_TRY(shatter_impl(ctx, h, in, steps, &S));
+  tr.mark("shatter");
   DevMerged &m = S.merged;
   BcInput bi;
   bi.row = m.mrow.p;
@@ -356,6 +365,7 @@ static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double 
   BcPlanOpts po;
   po.fp32_delta = o && o->delta_fp32;
   BCS_TRY(run_bcreach(ctx, S.comps, bi, po));
+  tr.mark("bcreach");
   DBuf<double> bc;
   double *d_bc = bc_out;
   if (!h->on_device) {
@@ -369,6 +379,7 @@ static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double 
     BCS_TRY(launch_mapback(ctx, m.nslots, m.slot_org.p, m.slot_to_m.p, m.mcorr.p, d_bc));
     ctx.stats.ms_mapback = tm.stop_ms();
   }
+  tr.mark("mapback");
   return output_bc(ctx, h, d_bc, bc_out);
 }
 

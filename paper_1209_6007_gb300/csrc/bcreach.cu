@@ -34,6 +34,7 @@
 #include <map>
 #include <mutex>
 #include <numeric>
+#include <set>
 
 #include "bc_math.cuh"
 #include "common.h"
@@ -613,13 +614,42 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
 static size_t large_scratch_bytes(int64_t nmax) { return (size_t)nmax * (4 + 4 + 8 + 8 + 8) + (size_t)(nmax + 2) * 8; }
 
 // ---------------------------------------------------------- host side
+// The shared-memory kernel's attribute (opt-in shared memory) and its
+// occupancy per shared-memory size are queried once per device and cached:
+// each query is a driver call on the host's critical path.
+static std::mutex g_small_mu;
+static std::map<long long, int> g_small_occ;  // (variant, device, smem) -> CTAs per SM
+
+template <bool R, bool I, bool F>
+static int small_prepare(int device) {
+  static std::mutex mu;
+  static std::set<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done.count(device)) {
+    BCS_CUDA(cudaFuncSetAttribute(k_bcreach_small<R, I, F>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)SMALL_SMEM));
+    done.insert(device);
+  }
+  return BCS_OK;
+}
+
 // CTAs of the shared-memory kernel that fit on one SM with `smem` bytes each
 template <bool R, bool I, bool F>
-static int small_ctas_per_sm(size_t smem, int *out) {
-  auto kern = k_bcreach_small<R, I, F>;
-  BCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM));
-  BCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, kern, SMALL_THREADS, smem));
+static int small_ctas_per_sm(int device, size_t smem, int *out) {
+  const long long key = ((long long)(R * 4 + I * 2 + F) << 48) | ((long long)device << 32) | (long long)smem;
+  {
+    std::lock_guard<std::mutex> lk(g_small_mu);
+    auto it = g_small_occ.find(key);
+    if (it != g_small_occ.end()) {
+      *out = it->second;
+      return BCS_OK;
+    }
+  }
+  BCS_TRY((small_prepare<R, I, F>(device)));
+  BCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_bcreach_small<R, I, F>, SMALL_THREADS, smem));
   if (*out < 1) *out = 1;
+  std::lock_guard<std::mutex> lk(g_small_mu);
+  g_small_occ[key] = *out;
   return BCS_OK;
 }
 
@@ -627,8 +657,8 @@ template <bool R, bool I, bool F>
 static int launch_small_t(Ctx &ctx, int grid, size_t smem, const SmallItem *items, int nitems, int *counter,
                           const CompDesc *comps, const BcInput &in, const int64_t *srcs, int32_t *lvl, int lvl_stride,
                           int *err, unsigned long long *dag) {
+  BCS_TRY((small_prepare<R, I, F>(ctx.device)));
   auto kern = k_bcreach_small<R, I, F>;
-  BCS_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMALL_SMEM));
   kern<<<grid, SMALL_THREADS, smem, ctx.stream>>>(items, nitems, counter, comps, in.row, in.col, in.reach, in.ident,
                                                  srcs, in.bcp, lvl, lvl_stride, err, dag);
   ctx.launches++;
@@ -684,6 +714,7 @@ static void remember_split(long long key, int choice) {
 }
 
 int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po) {
+  Tracer tr("bcreach", ctx.stream);
   const bool R = in.reach != nullptr, I = in.ident != nullptr, F = po.fp32_delta;
   const bool dbg = po.dbg_d || po.dbg_sig || po.dbg_exp || po.dbg_delta;
   const int64_t C = (int64_t)comps.size();
@@ -716,6 +747,11 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   // per CTA (the most that fit in SMALL_SMEM); the launch takes exactly the
   // shared memory its largest item needs, so occupancy follows the plan.
   // Items of similar cost go first-largest into a persistent queue.
+  // pieces by cost, largest first (ties in piece order), so that the
+  // persistent queue hands out the longest items first
+  std::stable_sort(small.begin(), small.end(), [&](int32_t a, int32_t b) {
+    return comps[a].nnz + comps[a].n > comps[b].nnz + comps[b].n;
+  });
   auto plan_small = [&](int ng_cap, size_t budget, std::vector<SmallItem> &out, size_t &smem, int &grid) -> int {
     out.clear();
     smem = 0;
@@ -732,7 +768,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
       smem = std::max(smem, small_smem_bytes(c.n, c.nnz, ng, R, I));
     }
     int per_sm = 1;
-    BCS_TRY(BCS_DISPATCH3(small_ctas_per_sm, R, I, F, smem, &per_sm));
+    BCS_TRY(BCS_DISPATCH3(small_ctas_per_sm, R, I, F, ctx.device, smem, &per_sm));
     grid = ctx.num_sms * per_sm;
     const double target = total_small_cost / (double)((int64_t)grid * SMALL_MAX_GROUPS) + 1.0;
     for (size_t k = 0; k < small.size(); k++) {
@@ -744,9 +780,6 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
       for (int64_t b = 0; b < ns; b += chunk)
         out.push_back(SmallItem{small[k], (int32_t)b, (int32_t)std::min<int64_t>(ns, b + chunk), ng});
     }
-    std::stable_sort(out.begin(), out.end(), [&](const SmallItem &a, const SmallItem &b) {
-      return comps[a.comp].nnz + comps[a.comp].n > comps[b.comp].nnz + comps[b.comp].n;
-    });
     grid = (int)std::min<int64_t>(grid, (int64_t)out.size());
     return BCS_OK;
   };
@@ -773,11 +806,26 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     }
   };
   if (!use_ms) build_work();
+  tr.mark("classify");
   int ng_cap = SMALL_MAX_GROUPS;
   size_t budget = SMALL_SMEM;
   size_t smem_small = 0;
   int grid_small = 0;
+  // the autotuner's choice for this shape bucket, if it has one already
+  long long tune_key = 0;
+  int tuned = 0;
+  if (ctx.autotune && !small.empty()) {
+    const int kb = 64 - __builtin_clzll((unsigned long long)std::max<int64_t>(nmax_small, 1));
+    const int wb = (int)std::log2(std::max(total_small_cost, 1.0));
+    tune_key = ((long long)(R * 4 + I * 2 + F) << 40) | ((long long)kb << 20) | (long long)wb;
+    tuned = tuned_split(tune_key);
+    if (tuned) {
+      ng_cap = TUNE_SPLITS[tuned - 1].ng_cap;
+      budget = TUNE_SPLITS[tuned - 1].budget;
+    }
+  }
   if (!small.empty()) BCS_TRY(plan_small(ng_cap, budget, items, smem_small, grid_small));
+  tr.mark("plan0");
   ctx.stats.n_small_items = (int64_t)items.size();
   ctx.stats.n_large_sources = 0;
   for (int32_t ci : large) ctx.stats.n_large_sources += po.sources ? po.nsources : comps[ci].n;
@@ -799,6 +847,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     BCS_TRY(d_srcs.alloc(po.nsources, ctx.stream));
     BCS_CUDA(cudaMemcpyAsync(d_srcs.p, po.sources, po.nsources * sizeof(int64_t), cudaMemcpyHostToDevice, ctx.stream));
   }
+  tr.mark("upload");
   if (!items.empty()) {
     StageTimer tm(ctx.stream);
     tm.start();
@@ -818,14 +867,12 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
       return BCS_DISPATCH3(launch_small_t, R, I, F, ctx, grid, smem, d_items.p, (int)its.size(), d_err.p + 1,
                            d_comps.p, tin, po.sources ? d_srcs.p : nullptr, lvl.p, lvl_stride, d_err.p, d_dag.p);
     };
-    if (ctx.autotune) {
+    tr.mark("alloc");
+    if (ctx.autotune && tuned == 0) {
       // tune once per shape bucket: time each split into a scratch
       // accumulator and keep the fastest
-      const int kb = 64 - __builtin_clzll((unsigned long long)std::max<int64_t>(nmax_small, 1));
-      const int wb = (int)std::log2(std::max(total_small_cost, 1.0));
-      const long long key = ((long long)(R * 4 + I * 2 + F) << 40) | ((long long)kb << 20) | (long long)wb;
-      int best = tuned_split(key);
-      if (best == 0) {
+      int best = 0;
+      {
         int64_t ntot = 0;
         for (const CompDesc &c : comps) ntot = std::max<int64_t>(ntot, c.vtx_off + c.n);
         DBuf<double> scratch;
@@ -850,7 +897,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
           }
         }
         BCS_CUDA(cudaMemsetAsync(d_dag.p, 0, sizeof(unsigned long long), ctx.stream));
-        remember_split(key, best);
+        remember_split(tune_key, best);
       }
       ng_cap = TUNE_SPLITS[best - 1].ng_cap;
       budget = TUNE_SPLITS[best - 1].budget;
@@ -858,10 +905,12 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
       ctx.stats.n_small_items = (int64_t)items.size();
       tm.start();
     }
+    tr.mark("plan");
     ctx.stats.small_ng_cap = ng_cap;
     ctx.stats.small_smem_budget = (int64_t)budget;
     BCS_TRY(run_small(items, smem_small, grid_small, in.bcp));
     ctx.stats.ms_bcreach_small += tm.stop_ms();
+    tr.mark("small");
   }
   if (use_ms) {
     StageTimer tm(ctx.stream);

@@ -106,12 +106,15 @@ struct StageTimer {
 
 // Optional per-stage trace: with the environment variable BCS_TRACE set,
 // marks are CUDA events on the call's stream and the gaps between them are
-// printed to stderr when the tracer goes out of scope.
+// printed to stderr when the tracer goes out of scope, each with the host
+// time that passed between the same marks (a host step shows up as GPU time
+// well below host time).
 struct Tracer {
   const char *scope;
   cudaStream_t s;
   bool on;
   std::vector<std::pair<const char *, cudaEvent_t>> marks;
+  std::vector<double> host_ms;  // host clock at each mark
   Tracer(const char *scope_name, cudaStream_t stream);
   ~Tracer();
   void mark(const char *name);
@@ -165,7 +168,6 @@ struct DevMerged {
   std::vector<int64_t> h_piece_off;  // host copies for planning
   std::vector<int64_t> h_piece_ent;  // entries per piece
   std::vector<int32_t> h_piece_maxdeg;  // largest degree per piece before merging
-  int32_t max_ident = 1;
 };
 
 int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out);

@@ -230,6 +230,7 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
   out->piece_N.swap(pc.piece_N);
   const int block = 256;
   const int gs = grid_for(S, block, ctx.num_sms * 32);
+  Tracer tr("merge", ctx.stream);
 
   DBuf<int32_t> cls, cnt;
   DBuf<int8_t> typ;
@@ -265,6 +266,7 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
     k_iota32<<<gs, block, 0, ctx.stream>>>(S, cls.p);
     ctx.launches++;
   }
+  tr.mark("classes");
   // compaction
   DBuf<int64_t> keep, ndeg, mslot, mrow_scan, totals;
   BCS_TRY(keep.alloc(S, ctx.stream));
@@ -282,6 +284,7 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
   BCS_CUDA(cudaMemcpyAsync(h_tot, totals.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
   BCS_CUDA(cudaStreamSynchronize(ctx.stream));
   const int64_t M = h_tot[0], ME = h_tot[1];
+  tr.mark("sizes");
   out->nmerged = M;
   out->nentries = ME;
   BCS_TRY(out->mrow.alloc(M + 1, ctx.stream));
@@ -300,6 +303,7 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
                                                out->mreach.p, out->mident.p, out->mcorr.p, out->slot_to_m.p);
     ctx.launches++;
   }
+  tr.mark("emit");
   DBuf<int64_t> prow;
   BCS_TRY(prow.alloc(P + 1, ctx.stream));
   k_piece_bounds<<<grid_for(P + 1, block, ctx.num_sms * 8), block, 0, ctx.stream>>>(P, piece_off, mslot.p, M,
@@ -316,17 +320,8 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
   if (P)
     BCS_CUDA(cudaMemcpyAsync(out->h_piece_maxdeg.data(), pc.piece_maxdeg.p, P * sizeof(int32_t),
                              cudaMemcpyDeviceToHost, ctx.stream));
-  if (identical && S > 0) {
-    // largest ident, for the path-count growth bound of the Bc-Reach kernels
-    std::vector<int32_t> hc(S);
-    BCS_CUDA(cudaMemcpyAsync(hc.data(), cnt.p, S * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
-    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
-    int32_t mx = 1;
-    for (int32_t c : hc) mx = c > mx ? c : mx;
-    out->max_ident = mx;
-  } else {
-    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
-  }
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  tr.mark("tables");
   out->h_piece_ent.resize(P);
   for (int64_t p = 0; p < P; p++) out->h_piece_ent[p] = hrow[p + 1] - hrow[p];
   return BCS_OK;
