@@ -29,6 +29,23 @@ __device__ __forceinline__ void split_pow2(double x, int &e, float &m) {
   }
 }
 
+// (double)x for 0 < x < 2^63, rounded to nearest even, built from integer
+// instructions only (the hardware conversion issues on GB300's FP64 pipe).
+__device__ __forceinline__ double i64_to_f64_pos(long long x) {
+  const unsigned long long u = (unsigned long long)x;
+  const int e = 63 - __clzll(x);  // floor(log2 x)
+  unsigned long long m;           // 53-bit significand with the leading one
+  if (e <= 52) {
+    m = u << (52 - e);
+  } else {
+    const int sh = e - 52;
+    m = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+    m += (rem > half || (rem == half && (m & 1ull))) ? 1ull : 0ull;  // a carry to 2^53 bumps the exponent
+  }
+  return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) + (m - (1ull << 52))));
+}
+
 // ceil(log2 x) for x >= 1 from the bit pattern (integer instructions only)
 __device__ __forceinline__ int ceil_log2_pos(double x) {
   const long long b = __double_as_longlong(x);

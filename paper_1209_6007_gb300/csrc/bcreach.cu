@@ -329,7 +329,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
       const int32_t v = st.queue[i];
       double dv;
       if (!FP32) {
-        const double sv = is_int ? (double)sigi[v] : sig[v];
+        const double sv = is_int ? i64_to_f64_pos(sigi[v]) : sig[v];
         double sum = 0.0;
         if (l < Lmax) {
           // successors first as a bit mask (integer work), then FP64 adds

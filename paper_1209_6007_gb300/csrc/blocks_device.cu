@@ -410,13 +410,17 @@ __global__ void k_slot_degrees(int64_t cnt, const int32_t *__restrict__ verts, b
                                const int32_t *__restrict__ top_slot, int64_t *sdeg) {
   GRID_STRIDE(i, cnt) {
     const int32_t v = verts[i];
+    const int32_t hs = home_slot[v];  // most of v's entries go to its home slot: counted in a register
+    int64_t nh = 0;
     for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
       const int32_t w = col[k];
       if (!alive[w]) continue;
       int32_t sv, sw;
       edge_slots(art, v, w, parent, level, bid, home_slot, top_slot, sv, sw);
-      sdeg[sv]++;  // every slot of v is written only by v's thread
+      if (sv == hs) nh++;
+      else sdeg[sv]++;  // every slot of v is written only by v's thread
     }
+    if (nh > 0) sdeg[hs] += nh;  // nh > 0 implies a home slot
   }
 }
 
@@ -427,12 +431,15 @@ __global__ void k_slot_fill(int64_t cnt, const int32_t *__restrict__ verts, bool
                             const int32_t *__restrict__ top_slot, int64_t *cursor, int32_t *scol) {
   GRID_STRIDE(i, cnt) {
     const int32_t v = verts[i];
+    const int32_t hs = home_slot[v];
+    int64_t hpos = hs >= 0 ? cursor[hs] : 0;  // the home slot's cursor stays in a register
     for (int64_t k = rp[v]; k < rp[v + 1]; k++) {
       const int32_t w = col[k];
       if (!alive[w]) continue;
       int32_t sv, sw;
       edge_slots(art, v, w, parent, level, bid, home_slot, top_slot, sv, sw);
-      scol[cursor[sv]++] = sw;
+      if (sv == hs) scol[hpos++] = sw;
+      else scol[cursor[sv]++] = sw;
     }
   }
 }
@@ -461,6 +468,7 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
   BCS_TRY(parent.alloc(n, ctx.stream));
   BCS_TRY(bid.alloc(n, ctx.stream));
   BCS_TRY(home_slot.alloc(n, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(home_slot.p, 0xFF, n * sizeof(int32_t), ctx.stream));  // -1: no home copy (roots)
   BCS_TRY(flag.alloc(n, ctx.stream));
   BCS_TRY(fscan.alloc(n, ctx.stream));
   BCS_TRY(tot.alloc(2, ctx.stream));
