@@ -747,11 +747,26 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   // per CTA (the most that fit in SMALL_SMEM); the launch takes exactly the
   // shared memory its largest item needs, so occupancy follows the plan.
   // Items of similar cost go first-largest into a persistent queue.
-  // pieces by cost, largest first (ties in piece order), so that the
-  // persistent queue hands out the longest items first
-  std::stable_sort(small.begin(), small.end(), [&](int32_t a, int32_t b) {
-    return comps[a].nnz + comps[a].n > comps[b].nnz + comps[b].n;
-  });
+  // pieces by cost class (the power of two of n + nnz), largest first, in
+  // piece order within a class: the persistent queue hands out the longest
+  // items first.  A counting sort: one pass, no comparisons.
+  {
+    int64_t cnt[65] = {0};
+    std::vector<int32_t> cls(small.size());
+    for (size_t k = 0; k < small.size(); k++) {
+      const CompDesc &c = comps[small[k]];
+      cls[k] = 63 - __builtin_clzll((unsigned long long)(c.nnz + c.n) | 1ull);
+      cnt[cls[k]]++;
+    }
+    int64_t off[65], o = 0;
+    for (int b = 64; b >= 0; b--) {
+      off[b] = o;
+      o += cnt[b];
+    }
+    std::vector<int32_t> sorted(small.size());
+    for (size_t k = 0; k < small.size(); k++) sorted[off[cls[k]]++] = small[k];
+    small.swap(sorted);
+  }
   auto plan_small = [&](int ng_cap, size_t budget, std::vector<SmallItem> &out, size_t &smem, int &grid) -> int {
     out.clear();
     smem = 0;
@@ -784,11 +799,19 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     return BCS_OK;
   };
   // Large pieces: 32 sources per CTA when there are enough batches to give
-  // every SM two of them, else one source per CTA (more CTAs in flight).
+  // every SM two of them and their scratch fits at least one CTA per SM,
+  // else one source per CTA (more CTAs in flight).
   // BCS_LARGE_PATH=batched|per_source overrides the choice.
   int64_t nbatches = 0;
   for (int32_t ci : large) nbatches += ((po.sources ? po.nsources : comps[ci].n) + 31) / 32;
   bool use_ms = !large.empty() && !dbg && !po.per_source_large && nbatches >= 2 * (int64_t)ctx.num_sms;
+  if (use_ms) {
+    // its per-CTA scratch grows with the piece: with fewer CTAs than SMs the
+    // batches serialise (high-diameter graphs of millions of vertices)
+    int64_t fit = 0;
+    BCS_TRY(ms_ctas_that_fit(nmax_large, &fit));
+    if (fit < ctx.num_sms) use_ms = false;
+  }
   if (!large.empty() && !dbg && !po.per_source_large) {
     if (const char *e = std::getenv("BCS_LARGE_PATH")) {
       if (!std::strcmp(e, "batched")) use_ms = true;

@@ -222,6 +222,9 @@ struct BcPlanOpts {
 // Bc-Reach with 32 sources per CTA over the listed (large) components;
 // *depth_failed reports a graph too deep for its level index (nothing is
 // then added to in.bcp).
+// CTAs of the 32-source kernel whose global scratch fits in half of the free
+// device memory, for pieces of at most nmax vertices
+int ms_ctas_that_fit(int64_t nmax, int64_t *out);
 int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32_t> &large, const BcInput &in,
            bool fp32, const int64_t *sources, int64_t nsources, const CompDesc *d_comps, int *d_err,
            unsigned long long *d_dag, bool *depth_failed);

@@ -382,6 +382,20 @@ static int launch_ms_t(Ctx &ctx, int grid, const MsBatch *batches, int nbatch, i
        : ((I) ? ((F) ? launch_ms_t<false, true, true>(__VA_ARGS__) : launch_ms_t<false, true, false>(__VA_ARGS__)) \
               : ((F) ? launch_ms_t<false, false, true>(__VA_ARGS__) : launch_ms_t<false, false, false>(__VA_ARGS__))))
 
+// global scratch of one 32-source CTA over pieces of at most nmax vertices
+static size_t ms_bytes_per_cta(int64_t nmax) {
+  const int64_t qcap = 32 * nmax + 32;
+  return (size_t)nmax * (4 + 4 + 8 + 8 + 256) + (size_t)qcap * 8 + (size_t)(MS_LCAP + 2) * 4 +
+         (size_t)MS_LCAP * 32 * 4;
+}
+
+int ms_ctas_that_fit(int64_t nmax, int64_t *out) {
+  size_t free_b = 0, total_b = 0;
+  BCS_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  *out = (int64_t)(free_b / 2 / ms_bytes_per_cta(nmax));
+  return BCS_OK;
+}
+
 int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32_t> &large, const BcInput &in,
            bool fp32, const int64_t *sources, int64_t nsources, const CompDesc *d_comps, int *d_err,
            unsigned long long *d_dag, bool *depth_failed) {
@@ -404,8 +418,7 @@ int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32
     for (int64_t i = 0; i < nsources; i++) hsrc[i] = (int32_t)sources[i];
   }
   const int64_t qcap = 32 * nmax + 32;
-  const size_t per = (size_t)nmax * (4 + 4 + 8 + 8 + 256) + (size_t)qcap * 8 + (size_t)(MS_LCAP + 2) * 4 +
-                     (size_t)MS_LCAP * 32 * 4;
+  const size_t per = ms_bytes_per_cta(nmax);
   size_t free_b = 0, total_b = 0;
   BCS_CUDA(cudaMemGetInfo(&free_b, &total_b));
   int64_t grid = std::min<int64_t>((int64_t)ctx.num_sms * 2, (int64_t)batches.size());
