@@ -90,6 +90,16 @@ struct CoefT<true> {
   using type = Coef32;
 };
 
+// Reciprocals 1/k of the integers k < RECIP_TABLE (entry 0 unused), filled
+// once per device by IEEE division (correctly rounded).
+constexpr int RECIP_TABLE = 1024;
+static __device__ double g_recip_table[RECIP_TABLE];
+
+__global__ void k_fill_recip_table() {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < RECIP_TABLE; k += gridDim.x * blockDim.x)
+    g_recip_table[k] = k == 0 ? 0.0 : 1.0 / (double)k;
+}
+
 // State of one source, in shared (small path) or global (large path) memory.
 template <bool FP32>
 struct SrcState {
@@ -329,7 +339,8 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
       const int32_t v = st.queue[i];
       double dv;
       if (!FP32) {
-        const double sv = is_int ? i64_to_f64_pos(sigi[v]) : sig[v];
+        const long long si = is_int ? sigi[v] : 0;
+        const double sv = is_int ? i64_to_f64_pos(si) : sig[v];
         double sum = 0.0;
         if (l < Lmax) {
           // successors first as a bit mask (integer work), then FP64 adds
@@ -358,7 +369,13 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
         dv = fma(sv, sum, init);
         if (l > 0) {  // the source's coefficient is never read
           const double kv = IDENT ? (wt.ident_d ? wt.ident_d[v] : (double)wt.ident[v]) : 1.0;
-          ((double *)st.coef)[v] = fma(kv, dv, kv) * recip_pos(sv);
+          // 1/sigma: small integer counts (the usual case) from a table of
+          // correctly rounded reciprocals, so a warp whose lanes all have one
+          // issues no FP64 work for it
+          double r;
+          if (PUSH && is_int && si < RECIP_TABLE) r = g_recip_table[si];
+          else r = recip_pos(sv);
+          ((double *)st.coef)[v] = fma(kv, dv, kv) * r;
         }
       } else {
         int ev;
@@ -633,6 +650,21 @@ static int small_prepare(int device) {
   return BCS_OK;
 }
 
+// The reciprocal table, filled once per device (on the legacy stream, which
+// orders it before any later work of every blocking stream).
+static int recip_table_ready(int device) {
+  static std::mutex mu;
+  static std::set<int> done;
+  std::lock_guard<std::mutex> lk(mu);
+  if (!done.count(device)) {
+    k_fill_recip_table<<<4, 256>>>();
+    BCS_CUDA(cudaGetLastError());
+    BCS_CUDA(cudaDeviceSynchronize());
+    done.insert(device);
+  }
+  return BCS_OK;
+}
+
 // CTAs of the shared-memory kernel that fit on one SM with `smem` bytes each
 template <bool R, bool I, bool F>
 static int small_ctas_per_sm(int device, size_t smem, int *out) {
@@ -658,6 +690,7 @@ static int launch_small_t(Ctx &ctx, int grid, size_t smem, const SmallItem *item
                           const CompDesc *comps, const BcInput &in, const int64_t *srcs, int32_t *lvl, int lvl_stride,
                           int *err, unsigned long long *dag) {
   BCS_TRY((small_prepare<R, I, F>(ctx.device)));
+  BCS_TRY(recip_table_ready(ctx.device));
   auto kern = k_bcreach_small<R, I, F>;
   kern<<<grid, SMALL_THREADS, smem, ctx.stream>>>(items, nitems, counter, comps, in.row, in.col, in.reach, in.ident,
                                                  srcs, in.bcp, lvl, lvl_stride, err, dag);
