@@ -53,7 +53,7 @@ struct SmallItem {
   int32_t comp;
   int32_t s_begin;  // index range into the source list (or local ids)
   int32_t s_end;
-  int32_t ngroups;  // groups per CTA (1, 2, 4, 8)
+  int32_t ngroups;  // groups (concurrent sources) per CTA, 1..8
 };
 
 // ------------------------------------------------------------------ group
@@ -522,8 +522,11 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
       a[v] = 0.0;
     }
     __syncthreads();
-    const int gsize = SMALL_THREADS / ng;
+    // whole warps per group; with ng not dividing the CTA's warps the
+    // remaining warps sit out this item
+    const int gsize = 32 * ((SMALL_THREADS / 32) / ng);
     const int gid = tid / gsize;
+    const bool in_group = gid < ng;
     Group g{tid % gsize, gsize, 1 + gid};
     unsigned char *q = p + per * gid;
     SrcState<FP32> st;
@@ -543,7 +546,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.qtail = &s_qtail[gid];
     st.red = s_red[gid];
     Weights wt{reach, ident, init_d, ident_d};
-    for (int i = item.s_begin + gid; i < item.s_end; i += ng) {
+    for (int i = item.s_begin + gid; in_group && i < item.s_end; i += ng) {
       const int32_t s = srcs ? (int32_t)srcs[i] : i;
       bcreach_source<REACH, IDENT, FP32, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr, dag);
     }
@@ -807,7 +810,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     for (size_t k = 0; k < small.size(); k++) {
       const CompDesc &c = comps[small[k]];
       int ng = 1;  // a piece that does not fit the budget even alone still runs (up to SMALL_SMEM)
-      for (int cand = ng_cap; cand >= 1; cand >>= 1)
+      for (int cand = ng_cap; cand >= 1; cand--)
         if (small_smem_bytes(c.n, c.nnz, cand, R, I) <= budget) {
           ng = cand;
           break;
