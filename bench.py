@@ -299,7 +299,8 @@ def run_ours(args):
     t32 = ev0.elapsed_time(ev1) / 1e3
     ref = bc.double()
     err32 = float((b32 - ref).abs().max() / max(1.0, float(ref.abs().max())))
-    fp32 = {"gteps": nm / t32 / 1e9, "rel_err_vs_fp64": err32}
+    fp32 = {"gteps": nm / t32 / 1e9, "rel_err_vs_fp64": err32,
+            "speedup_vs_plain_fp64": (nm / t32 / 1e9 / plain["gteps"]) if plain else None}
 
     # roofline of the dominant kernel (Bc-Reach, shared-memory path): it is
     # bound by GB300's FP64 pipe, so the figure is algorithmic FP64 FLOP/s:

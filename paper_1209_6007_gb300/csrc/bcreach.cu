@@ -10,17 +10,17 @@
 // Phase 2 is evaluated in the equivalent "coefficient" form
 //     c[w] = k[w] (1 + delta[w]) / sigma[w],   delta[v] = r[v] - 1 + sigma[v] * sum_w c[w]
 // so that each shortest-path-DAG edge costs one addition and each vertex one
-// division.
+// reciprocal (from a table for small integer counts).
 //
 // A group of threads (one warp up to a whole CTA) runs one source at a time,
 // level-synchronously: the BFS queue doubles as the stack of Algorithm 1 and
 // its level boundaries are kept, so phase 2 walks the levels deepest first
 // and pulls from the successors (no atomics in phase 2).
 //
-// Path counts.  sigma is FP64.  Each level carries a power-of-two exponent:
-// when a level's largest count passes 2^960 the whole level is scaled by an
-// exact power of two, and phase 2 multiplies by 2^(e[L] - e[L+1]).  Counts
-// below 2^53 are never scaled and stay exact integers.
+// Path counts are exact 64-bit integers while a level's growth bound stays
+// below 2^62; past it they are FP64 and each level carries a power-of-two
+// exponent: when a level's largest count passes 2^960 the whole level is
+// scaled by an exact power of two, and phase 2 multiplies by 2^(e[L] - e[L+1]).
 //
 // FP32 mode keeps delta and the per-edge sums in FP32: c is stored as an FP32
 // value relative to the binary exponent of sigma[w] (held next to it), so
@@ -450,8 +450,9 @@ __host__ __device__ inline size_t small_group_bytes(int64_t n) {
 }
 
 // bytes of shared memory a component needs with `ng` concurrent sources:
-// the component (rows, columns, reach, ident) once, and per group the
-// distances, queue, path counts, coefficients and its own bc accumulator
+// the component (rows, columns, reach and ident with their FP64 copies) once,
+// and per group the distances, queue, DAG masks, path counts / coefficients
+// and its own bc accumulator
 __host__ __device__ inline size_t small_smem_bytes(int64_t n, int64_t nnz, int ng, bool reach, bool ident) {
   size_t b = align16((size_t)(n + 1) * 4) + align16((size_t)nnz * 4);
   if (reach) b += align16((size_t)n * 4) + align16((size_t)n * 8);
@@ -911,7 +912,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     StageTimer tm(ctx.stream);
     tm.start();
     const int lvl_stride = (int)nmax_small + 2;
-    const size_t grid_cap = (size_t)ctx.num_sms * (SMALL_THREADS * 8 / SMALL_THREADS);  // 8 CTAs/SM at most
+    const size_t grid_cap = (size_t)ctx.num_sms * (2048 / SMALL_THREADS);  // resident CTAs per SM at most
     DBuf<int32_t> lvl;
     BCS_TRY(lvl.alloc(grid_cap * SMALL_MAX_GROUPS * lvl_stride * 2, ctx.stream));
     DBuf<SmallItem> d_items;
