@@ -48,6 +48,8 @@ constexpr size_t SMALL_SMEM = 100 * 1024;
 constexpr int SMALL_MAX_GROUPS = 8;
 constexpr int DISC_CH = 4;  // row entries per step of the shared-memory discovery pass (divides 32)
 constexpr int LARGE_THREADS = 512;
+// BFS depth above which large pieces run one source per CTA rather than 32
+constexpr int MS_DEPTH_LIMIT = 64;
 
 struct SmallItem {
   int32_t comp;
@@ -161,7 +163,7 @@ template <bool REACH, bool IDENT, bool FP32, bool RESET_BY_QUEUE, typename RowT,
 __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n, const RowT *__restrict__ row,
                                const ColT *__restrict__ col, const Weights wt, const SrcState<FP32> st,
                                double *acc, const double fan, int *err, const Debug *dbg,
-                               unsigned long long &dag) {
+                               unsigned long long &dag, int *lmax_out = nullptr) {
   int32_t *const d = st.d;
   double *const sig = st.sig;
   long long *const sigi = (long long *)st.sig;
@@ -323,6 +325,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
     }
   }
   const int Lmax = L;
+  if (lmax_out && g.rank == 0) atomicMax(lmax_out, Lmax);
   // the source's weight reach[s] * ident[s] waits in shared memory: read
   // per vertex, it is never recomputed (FP64) inside the divergent loop
   if (g.rank == 0)
@@ -588,7 +591,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
     const LargeSrc *__restrict__ work, int64_t nwork, unsigned long long *counter, const CompDesc *__restrict__ comps,
     const int64_t *__restrict__ g_row, const int32_t *__restrict__ g_col, const int32_t *__restrict__ g_reach,
     const int32_t *__restrict__ g_ident, double *bcp, LargeScratch sc, int *err, Debug dbg_in, int use_dbg,
-    unsigned long long *dag_total) {
+    unsigned long long *dag_total, int *lmax) {
   __shared__ unsigned long long s_idx;
   __shared__ int s_qtail;
   __shared__ double s_red[16];
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
     const CompDesc c = comps[cur];
     Weights wt{REACH ? g_reach + c.vtx_off : nullptr, IDENT ? g_ident + c.vtx_off : nullptr, nullptr, nullptr};
     bcreach_source<REACH, IDENT, FP32, true>(g, work[idx].s, c.n, g_row + c.row_off, g_col, wt, st, acc, c.fan, err,
-                                             use_dbg ? &dbg_in : nullptr, dag);
+                                             use_dbg ? &dbg_in : nullptr, dag, lmax);
   }
   if (dag_total && dag) atomicAdd(dag_total, dag);
 }
@@ -706,10 +709,10 @@ static int launch_small_t(Ctx &ctx, int grid, size_t smem, const SmallItem *item
 template <bool R, bool I, bool F>
 static int launch_large_t(Ctx &ctx, int grid, const LargeSrc *work, int64_t nwork, unsigned long long *counter,
                           const CompDesc *comps, const BcInput &in, const LargeScratch &sc, int *err,
-                          const Debug &dbg, int use_dbg, unsigned long long *dag) {
+                          const Debug &dbg, int use_dbg, unsigned long long *dag, int *lmax = nullptr) {
   k_bcreach_large<R, I, F><<<grid, LARGE_THREADS, 0, ctx.stream>>>(work, nwork, counter, comps, in.row, in.col,
                                                                   in.reach, in.ident, in.bcp, sc, err, dbg, use_dbg,
-                                                                  dag);
+                                                                  dag, lmax);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;
@@ -849,23 +852,28 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     BCS_TRY(ms_ctas_that_fit(nmax_large, &fit));
     if (fit < ctx.num_sms) use_ms = false;
   }
+  bool forced = false;  // BCS_LARGE_PATH=batched|per_source overrides the choice
   if (!large.empty() && !dbg && !po.per_source_large) {
     if (const char *e = std::getenv("BCS_LARGE_PATH")) {
-      if (!std::strcmp(e, "batched")) use_ms = true;
-      if (!std::strcmp(e, "per_source")) use_ms = false;
+      if (!std::strcmp(e, "batched")) use_ms = forced = true;
+      if (!std::strcmp(e, "per_source")) {
+        use_ms = false;
+        forced = true;
+      }
     }
   }
-  // the one-source-per-CTA list for large pieces (debug output, or the
+  // the one-source-per-CTA list for large pieces, from the `skip`-th source
+  // of each piece on (debug output, the depth probe's remainder, or the
   // fallback when a graph is too deep for the 32-source kernel)
-  auto build_work = [&]() {
+  auto build_work = [&](int64_t skip) {
     work.clear();
     for (int32_t ci : large) {
       const int64_t ns = po.sources ? po.nsources : comps[ci].n;
-      for (int64_t i = 0; i < ns; i++)
+      for (int64_t i = skip; i < ns; i++)
         work.push_back(LargeSrc{ci, (int32_t)(po.sources ? po.sources[i] : i)});
     }
   };
-  if (!use_ms) build_work();
+  if (!use_ms) build_work(0);
   tr.mark("classify");
   int ng_cap = SMALL_MAX_GROUPS;
   size_t budget = SMALL_SMEM;
@@ -972,22 +980,15 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     ctx.stats.ms_bcreach_small += tm.stop_ms();
     tr.mark("small");
   }
-  if (use_ms) {
-    StageTimer tm(ctx.stream);
-    tm.start();
-    bool depth_failed = false;
-    BCS_TRY(run_ms(ctx, comps, large, in, F, po.sources, po.nsources, d_comps.p, d_err.p, d_dag.p, &depth_failed));
-    if (depth_failed) build_work();
-    ctx.stats.ms_bcreach_large += tm.stop_ms();
-  }
-  if (!work.empty()) {
+  // one source per CTA over the given list; *d_lmax (optional) receives the
+  // deepest BFS level any of them reached
+  auto run_per_source = [&](const std::vector<LargeSrc> &w, int *d_lmax) -> int {
     StageTimer tm(ctx.stream);
     tm.start();
     DBuf<LargeSrc> d_work;
     DBuf<unsigned long long> counter;
-    BCS_TRY(d_work.alloc(work.size(), ctx.stream));
-    BCS_CUDA(cudaMemcpyAsync(d_work.p, work.data(), work.size() * sizeof(LargeSrc), cudaMemcpyHostToDevice,
-                             ctx.stream));
+    BCS_TRY(d_work.alloc(w.size(), ctx.stream));
+    BCS_CUDA(cudaMemcpyAsync(d_work.p, w.data(), w.size() * sizeof(LargeSrc), cudaMemcpyHostToDevice, ctx.stream));
     BCS_TRY(counter.alloc(1, ctx.stream));
     BCS_CUDA(cudaMemsetAsync(counter.p, 0, sizeof(unsigned long long), ctx.stream));
     // CTAs: up to 3 per SM, fewer when the scratch would take more than half
@@ -995,7 +996,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     size_t free_b = 0, total_b = 0;
     BCS_CUDA(cudaMemGetInfo(&free_b, &total_b));
     int64_t grid = (int64_t)ctx.num_sms * 3;
-    grid = std::min<int64_t>(grid, (int64_t)work.size());
+    grid = std::min<int64_t>(grid, (int64_t)w.size());
     const size_t per = large_scratch_bytes(nmax_large);
     if ((size_t)grid * per > free_b / 2) grid = std::max<int64_t>(1, (int64_t)(free_b / 2 / per));
     const size_t G = (size_t)grid, NM = (size_t)nmax_large;
@@ -1013,10 +1014,48 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     BCS_CUDA(cudaMemsetAsync(sacc.p, 0, G * NM * sizeof(double), ctx.stream));
     LargeScratch sc{sd.p, sq.p, ssig.p, scoef.p, sacc.p, sls.p, sle.p, (int64_t)NM};
     Debug dbgs{po.dbg_d, po.dbg_sig, po.dbg_exp, po.dbg_delta};
-    BCS_TRY(BCS_DISPATCH3(launch_large_t, R, I, F, ctx, (int)grid, d_work.p, (int64_t)work.size(), counter.p,
-                          d_comps.p, in, sc, d_err.p, dbgs, dbg ? 1 : 0, d_dag.p));
+    BCS_TRY(BCS_DISPATCH3(launch_large_t, R, I, F, ctx, (int)grid, d_work.p, (int64_t)w.size(), counter.p, d_comps.p,
+                          in, sc, d_err.p, dbgs, dbg ? 1 : 0, d_dag.p, d_lmax));
+    ctx.stats.ms_bcreach_large += tm.stop_ms();
+    return BCS_OK;
+  };
+  int64_t skip = 0;  // leading sources of each large piece already done
+  if (use_ms && !forced) {
+    // Depth probe: the first wave runs one source per CTA (useful work
+    // either way) and reports how deep its BFS went.  The 32-source kernel
+    // pays per BFS level and queues a vertex once per distinct level its
+    // sources reach it at, so on deep graphs (roads, grids) the remaining
+    // sources also run one per CTA.
+    const int64_t wave = (int64_t)ctx.num_sms * 3;
+    skip = std::max<int64_t>(1, wave / (int64_t)large.size());
+    std::vector<LargeSrc> probe;
+    for (int32_t ci : large) {
+      const int64_t ns = po.sources ? po.nsources : comps[ci].n;
+      for (int64_t i = 0; i < std::min(ns, skip); i++)
+        probe.push_back(LargeSrc{ci, (int32_t)(po.sources ? po.sources[i] : i)});
+    }
+    DBuf<int> d_lmax;
+    BCS_TRY(d_lmax.alloc(1, ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(d_lmax.p, 0, sizeof(int), ctx.stream));
+    BCS_TRY(run_per_source(probe, d_lmax.p));
+    int lmax = 0;
+    BCS_CUDA(cudaMemcpyAsync(&lmax, d_lmax.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+    if (lmax > MS_DEPTH_LIMIT) {
+      use_ms = false;
+      build_work(skip);
+    }
+  }
+  if (use_ms) {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    bool depth_failed = false;
+    BCS_TRY(run_ms(ctx, comps, large, in, F, po.sources, po.nsources, skip, d_comps.p, d_err.p, d_dag.p,
+                   &depth_failed));
+    if (depth_failed) build_work(skip);
     ctx.stats.ms_bcreach_large += tm.stop_ms();
   }
+  if (!work.empty()) BCS_TRY(run_per_source(work, nullptr));
   int h_err = 0;
   unsigned long long h_dag = 0;
   BCS_CUDA(cudaMemcpyAsync(&h_err, d_err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));

@@ -225,8 +225,9 @@ struct BcPlanOpts {
 // CTAs of the 32-source kernel whose global scratch fits in half of the free
 // device memory, for pieces of at most nmax vertices
 int ms_ctas_that_fit(int64_t nmax, int64_t *out);
+// skip: leading sources of every large piece that were already processed
 int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32_t> &large, const BcInput &in,
-           bool fp32, const int64_t *sources, int64_t nsources, const CompDesc *d_comps, int *d_err,
+           bool fp32, const int64_t *sources, int64_t nsources, int64_t skip, const CompDesc *d_comps, int *d_err,
            unsigned long long *d_dag, bool *depth_failed);
 
 // Plan and run Bc-Reach over the given components.  comps are host

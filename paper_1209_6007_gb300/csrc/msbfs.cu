@@ -397,7 +397,7 @@ int ms_ctas_that_fit(int64_t nmax, int64_t *out) {
 }
 
 int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32_t> &large, const BcInput &in,
-           bool fp32, const int64_t *sources, int64_t nsources, const CompDesc *d_comps, int *d_err,
+           bool fp32, const int64_t *sources, int64_t nsources, int64_t skip, const CompDesc *d_comps, int *d_err,
            unsigned long long *d_dag, bool *depth_failed) {
   *depth_failed = false;
   std::vector<MsBatch> batches;
@@ -407,7 +407,7 @@ int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32
     const CompDesc &c = comps[ci];
     nmax = std::max<int64_t>(nmax, c.n);
     const int64_t ns = sources ? nsources : c.n;
-    for (int64_t b = 0; b < ns; b += 32) {
+    for (int64_t b = skip; b < ns; b += 32) {
       const int cnt = (int)std::min<int64_t>(32, ns - b);
       batches.push_back(MsBatch{ci, (int32_t)(sources ? b : b), cnt, 0});
     }

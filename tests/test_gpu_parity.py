@@ -202,11 +202,40 @@ def test_articulation_full_size_sources_vs_oracle(gpu):
     assert rel(got, ref) <= TOL64
 
 
+@pytest.mark.parametrize("cfg", [3, 4], ids=["twins", "road"])
+def test_large_full_size_sources_vs_oracle(gpu, cfg):
+    """The twin-heavy (n = 970k) and road-like (n = 2.26M, diameter in the
+    thousands) workloads at full size: plain Brandes on 256 seeded sources
+    against the oracle's partial sums."""
+    g = gg.config(cfg)
+    rng = np.random.default_rng(0xB0C00000 + cfg)
+    src = rng.choice(g.n, size=256, replace=False)
+    ref = oracle.bc_sources(g, src)
+    assert rel(gpu.bc_sources(g.row_ptr, g.col, src), ref) <= TOL64
+
+
+@pytest.mark.parametrize("cfg,pct", [(3, 5), (4, 3)], ids=["twins-5pct", "road-3pct"])
+def test_shattered_matches_plain_above_oracle_scale(gpu, cfg, pct):
+    """Above the size the oracle finishes in seconds: shattered (FP64 and
+    FP32 dependencies) against plain Brandes, both on the GPU (Thm. 1)."""
+    g = gg.config(cfg, scale_pct=pct)
+    rp, col = on_device(g)
+    plain = gpu.bc_plain(rp, col).cpu().numpy()
+    assert rel(gpu.bc_shattered(rp, col).cpu().numpy(), plain) <= TOL64
+    assert rel(gpu.bc_shattered(rp, col, delta_fp32=True).cpu().numpy(), plain) <= TOL32
+
+
 # ------------------------------------------- 32-source batches, large pieces
-def test_batched_sources_disconnected_and_ragged(gpu):
-    """Pieces too large for shared memory run 32 sources per CTA; a source
-    list of 45 entries (a ragged last batch) with repeats, on a graph with
-    several components (most sources do not reach most vertices)."""
+LARGE_PATHS = ["batched", "per_source"]
+
+
+@pytest.mark.parametrize("path", LARGE_PATHS)
+def test_batched_sources_disconnected_and_ragged(gpu, path, monkeypatch):
+    """Pieces too large for shared memory run 32 sources per CTA (or one per
+    CTA; both kernels, forced); a source list of 45 entries (a ragged last
+    batch) with repeats, on a graph with several components (most sources do
+    not reach most vertices)."""
+    monkeypatch.setenv("BCS_LARGE_PATH", path)
     g = gg.disjoint_union(gg.config(1), gg.chung_lu(3000, 2.5, 5.0, 3), gg.cycle(700))
     rng = np.random.default_rng(11)
     src = np.concatenate([rng.choice(g.n, size=40, replace=False), [5, 5, 9, 9, 2600]])
@@ -216,9 +245,11 @@ def test_batched_sources_disconnected_and_ragged(gpu):
     assert rel(gpu.bc_plain(g.row_ptr, g.col), oracle.bc(g)) <= TOL64
 
 
-def test_batched_sources_path_counts_beyond_double(gpu):
+@pytest.mark.parametrize("path", LARGE_PATHS)
+def test_batched_sources_path_counts_beyond_double(gpu, path, monkeypatch):
     """Sources at and near the corners of a 700 x 700 grid: path counts reach
     2^1392, so each (level, source) pair of a batch gets its own exponent."""
+    monkeypatch.setenv("BCS_LARGE_PATH", path)
     side = 700
     g = gg.grid(side, side)
     src = [0, 1, side, side * side - 1, side * side - 2, (side // 2) * side + side // 2]
