@@ -34,7 +34,15 @@
  * Errors: every call returns BCS_OK (0) or a negative BCS_E* code;
  * bcs_last_error() gives a message for the calling thread's last failure.
  * Calls from several host threads are allowed; they share no mutable state
- * apart from the per-device memory pool.
+ * apart from the per-device memory pool and a few process-wide caches, each
+ * behind a lock: the autotuner's choices, kernel occupancies, and a table of
+ * reciprocals that the first Bc-Reach call on a device fills (one kernel
+ * launch and a device-wide synchronisation).
+ *
+ * Environment: BCS_TRACE (any value) prints per-stage timings to stderr;
+ * BCS_LARGE_PATH=batched|per_source forces the kernel used for pieces too
+ * large for shared memory (32 sources per CTA, or one), which is otherwise
+ * chosen from the number of sources, the memory it needs and the BFS depth.
  */
 #ifndef BCSHATTER_H
 #define BCSHATTER_H
