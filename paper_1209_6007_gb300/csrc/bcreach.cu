@@ -453,11 +453,11 @@ __host__ __device__ inline size_t small_group_bytes(int64_t n) {
 }
 
 // bytes of shared memory a component needs with `ng` concurrent sources:
-// the component (rows, columns, reach and ident with their FP64 copies) once,
+// the component (rows, 16-bit columns, reach and ident with their FP64 copies) once,
 // and per group the distances, queue, DAG masks, path counts / coefficients
 // and its own bc accumulator
 __host__ __device__ inline size_t small_smem_bytes(int64_t n, int64_t nnz, int ng, bool reach, bool ident) {
-  size_t b = align16((size_t)(n + 1) * 4) + align16((size_t)nnz * 4);
+  size_t b = align16((size_t)(n + 1) * 4) + align16((size_t)nnz * 2);
   if (reach) b += align16((size_t)n * 4) + align16((size_t)n * 8);
   if (ident) b += align16((size_t)n * 4) + align16((size_t)n * 8);
   return b + small_group_bytes(n) * (size_t)ng;
@@ -489,8 +489,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     unsigned char *p = smem;
     int32_t *row = (int32_t *)p;
     p += align16((size_t)(n + 1) * 4);
-    int32_t *col = (int32_t *)p;
-    p += align16((size_t)nnz * 4);
+    uint16_t *col = (uint16_t *)p;  // local ids of a shared-memory piece fit 16 bits
+    p += align16((size_t)nnz * 2);
     int32_t *reach = nullptr, *ident = nullptr;
     double *init_d = nullptr, *ident_d = nullptr;
     if (REACH) {
@@ -508,7 +508,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     const size_t per = small_group_bytes(n);
     const int64_t r0 = g_row[c.row_off];
     for (int v = tid; v <= n; v += SMALL_THREADS) row[v] = (int32_t)(g_row[c.row_off + v] - r0);
-    for (int e = tid; e < nnz; e += SMALL_THREADS) col[e] = g_col[r0 + e];
+    for (int e = tid; e < nnz; e += SMALL_THREADS) col[e] = (uint16_t)g_col[r0 + e];
     for (int v = tid; v < n; v += SMALL_THREADS) {
       if (REACH) {
         reach[v] = g_reach[c.vtx_off + v];
@@ -773,7 +773,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     const int64_t ns = po.sources ? po.nsources : c.n;
     work_se += (double)ns * (double)c.nnz;
     work_sv += (double)ns * (double)c.n;
-    const bool fits = !po.force_large && !dbg && small_smem_bytes(c.n, c.nnz, 1, R, I) <= SMALL_SMEM;
+    const bool fits = !po.force_large && !dbg && c.n <= 65535 && small_smem_bytes(c.n, c.nnz, 1, R, I) <= SMALL_SMEM;
     if (fits) {
       small.push_back((int32_t)ci);
       total_small_cost += (double)ns * (double)(c.nnz + c.n);
