@@ -48,6 +48,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="articulation", choices=["articulation", "batch"],
+                    help="batch: a secondary measurement of many independent graphs in one call "
+                         "(not the headline line)")
+    ap.add_argument("--batch-count", type=int, default=20000)
+    ap.add_argument("--batch-nmax", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -340,10 +345,63 @@ def run_ours(args):
         print(json.dumps(line))
 
 
+def run_batch(args):
+    """Uneven batch (the batched workload's generator with a bounded largest
+    graph): `--batch-count` independent Chung-Lu graphs of log-uniform sizes
+    16..`--batch-nmax`, packed in one CSR, all shattered and solved by one
+    bcs_bc_shattered_batch call per step.  Work = sum over the graphs of
+    n_i * m_i (every vertex a source in its own graph)."""
+    import torch
+    import graphgen as gg
+    import paper_1209_6007_gb300 as bcs
+    torch.cuda.set_device(0)
+    bcs.load()
+    g, off = gg.batch(args.batch_count, n_min=16, n_max=args.batch_nmax)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    n_i = np.diff(off).astype(np.float64)
+    m_i = (g.row_ptr[off[1:]] - g.row_ptr[off[:-1]]).astype(np.float64) / 2
+    work = float((n_i * m_i).sum())
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        bcs.bc_shattered_batch(off, rp, col)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    dev_ms, launches = 0.0, 0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        bcs.bc_shattered_batch(off, rp, col)
+        ev1.record(stream)
+        ev1.synchronize()
+        dev_ms += ev0.elapsed_time(ev1)
+        launches += int(bcs.last_stats()["kernel_launches"])
+    clk = clocks.stop()
+    st = bcs.last_stats()
+    T = dev_ms / 1e3
+    line = {"metric": "BC GTEPS (sum over the batch's graphs of sources*m / s)", "value": work * args.steps / T / 1e9,
+            "unit": "GTEPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"uneven batch: {args.batch_count} Chung-Lu graphs (gamma 2.3, mean degree 8), "
+                                   f"n log-uniform 16..{args.batch_nmax}", "n": int(g.n), "m": int(g.m),
+                       "sum_n_m": work, "l2": "flushed between timed steps (256 MB write)"},
+            "gpu_launches": launches, "clocks": clk,
+            "stages_ms": {k: v for k, v in st.items() if k.startswith("ms_")},
+            "pieces": st["n_pieces"], "large_sources": st["n_large_sources"],
+            "note": "secondary measurement; the headline line is --workload articulation"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "batch":
+        run_batch(args)
     else:
         run_ours(args)
 

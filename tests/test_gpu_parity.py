@@ -202,6 +202,17 @@ def test_articulation_full_size_sources_vs_oracle(gpu):
     assert rel(got, ref) <= TOL64
 
 
+def test_mid_size_piece(gpu):
+    """A piece of ~2,500 vertices: more shared memory than the small path
+    gives one source, so it runs on the global-memory path."""
+    g = gg.chung_lu(3000, 2.3, 8.0, 5)
+    ref = oracle.bc(g)
+    for fn in (gpu.bc_plain, gpu.bc_shattered):
+        for fp32, tol in ((False, TOL64), (True, TOL32)):
+            assert rel(fn(g.row_ptr, g.col, delta_fp32=fp32), ref) <= tol
+            assert gpu.last_stats()["n_large_sources"] > 0
+
+
 @pytest.mark.parametrize("cfg", [3, 4], ids=["twins", "road"])
 def test_large_full_size_sources_vs_oracle(gpu, cfg):
     """The twin-heavy (n = 970k) and road-like (n = 2.26M, diameter in the
