@@ -57,6 +57,15 @@ __device__ __forceinline__ double pow2_int(int k) {
   return k < -1022 ? 0.0 : __longlong_as_double((long long)(k + 1023) << 52);
 }
 
+// Integer part of a 64-bit path count: binary exponent and [1,2) mantissa
+// as FP32 (integer instructions only); x >= 1.
+__device__ __forceinline__ void split_pow2_i64(long long x, int &e, float &m) {
+  e = 63 - __clzll(x);
+  const unsigned long long u = (unsigned long long)x;
+  const unsigned long long mant = e >= 23 ? (u >> (e - 23)) : (u << (23 - e));
+  m = __int_as_float(0x3f800000 | (int)(mant & 0x7fffffull));
+}
+
 // 1/x for a positive double.  The mantissa m in [1,2) gets an FP32 hardware
 // reciprocal approximation r (relative error e = 1 - m r of about 2^-22),
 // refined by one third-order step of the series 1/m = r (1 + e + e^2 + ...):

@@ -131,14 +131,6 @@ struct Debug {
   double *delta;
 };
 
-// Integer part of a 64-bit path count: binary exponent and [1,2) mantissa
-// as FP32 (integer instructions only); x >= 1.
-__device__ __forceinline__ void split_pow2_i64(long long x, int &e, float &m) {
-  e = 63 - __clzll(x);
-  const unsigned long long u = (unsigned long long)x;
-  const unsigned long long mant = e >= 23 ? (u >> (e - 23)) : (u << (23 - e));
-  m = __int_as_float(0x3f800000 | (int)(mant & 0x7fffffull));
-}
 
 // One source of Bc-Reach over a component held as (row, col) with local ids.
 // RESET_BY_QUEUE: the distances start at -1 and are put back that way

@@ -9,8 +9,9 @@
 //         64-bit word.  Adjacent vertices are at most one level apart, so
 //         "w is on level L+1 for source b" is decided by the level mod 4
 //         (together with vis for sources that have not reached w),
-//   sc    32 FP64 values, lane b's path count (phase 1), then its phase-2
-//         coefficient (the path count is not needed any more by then),
+//   sc    32 values, lane b's path count (phase 1: exact int64 while the
+//         level's growth bound stays below 2^62, FP64 after), then its FP64
+//         phase-2 coefficient (the path count is not needed any more by then),
 // and the vertices of each level in a queue (a vertex is queued once per
 // level in which it gains sources, so at most 32 times).
 //
@@ -104,6 +105,7 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
   uint32_t *const nxt = S.nxt + B * S.nmax;
   uint64_t *const lv = S.lv + B * S.nmax;
   double *const sc = S.sc + B * S.nmax * 32;
+  long long *const sci = (long long *)sc;  // the same slots while a level's counts are integers
   double *const acc = S.acc + B * S.nmax;
   int32_t *const queue = S.queue + B * S.qcap;
   uint32_t *const qmask = S.qmask + B * S.qcap;
@@ -150,7 +152,7 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
     for (int i = warp; i < hi; i += MS_WARPS) {
       const int32_t v = queue[i];
       const uint32_t N = nxt[v];
-      if ((N >> lane) & 1u) sc[(size_t)v * 32 + lane] = 1.0;
+      if ((N >> lane) & 1u) sci[(size_t)v * 32 + lane] = 1;
       __syncwarp();
       if (lane == 0) {
         qmask[i] = N;
@@ -168,6 +170,13 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
     int lo = 0, L = 0;
     double bound = 1.0;
     bool depth_fail = false;
+    // Path counts are exact 64-bit integers while the level's growth bound
+    // (an integer power of two) stays below 2^62; the first level past it is
+    // pulled in FP64, widening the integers of the level before as it reads
+    // them (lint = first FP64 level).
+    int lint = MS_LCAP + 2;
+    const int flg = ceil_log2_pos(c.fan);
+    int blg = 0;
     // ------------------------------------------------------------ phase 1
     for (;;) {
       for (int i = lo + warp; i < hi; i += MS_WARPS) {
@@ -187,6 +196,9 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
         depth_fail = true;
         break;
       }
+      const bool int_next = lint > L + 1 && blg + flg < 62;  // level L+1 keeps integer counts
+      if (!int_next && lint > L + 1) lint = L + 1;          // the first FP64 level
+      const bool from_int = L < lint;                         // level L still holds integers
       // path counts of the newly reached (vertex, source) pairs; vis and lv
       // of the new level are written only after every pull has read them.
       // Neighbours are fetched 32 at a time (id, level word, reached mask in
@@ -196,6 +208,7 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
         const int32_t w = queue[i];
         const uint32_t N = nxt[w];
         double a = 0.0;
+        long long ai = 0;
         const int64_t eb = row[w], ee = row[w + 1];
         for (int64_t e0 = eb; e0 < ee; e0 += 32) {
           const int cnt = (int)min((int64_t)32, ee - e0);
@@ -210,14 +223,21 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
               const uint32_t m = __shfl_sync(0xffffffffu, mj, j);
               const int32_t v = __shfl_sync(0xffffffffu, vj, j);
               if ((m >> lane) & 1u) {
-                double x = sc[(size_t)v * 32 + lane];
-                if (IDENT && L > 0) x *= (double)ident[v];
-                a += x;
+                if (int_next) {
+                  ai += sci[(size_t)v * 32 + lane] * (IDENT && L > 0 ? (long long)ident[v] : 1ll);
+                } else {
+                  double x = from_int ? i64_to_f64_pos(sci[(size_t)v * 32 + lane]) : sc[(size_t)v * 32 + lane];
+                  if (IDENT && L > 0) x *= (double)ident[v];
+                  a += x;
+                }
               }
             }
           }
         }
-        if ((N >> lane) & 1u) sc[(size_t)w * 32 + lane] = a;
+        if ((N >> lane) & 1u) {
+          if (int_next) sci[(size_t)w * 32 + lane] = ai;
+          else sc[(size_t)w * 32 + lane] = a;
+        }
       }
       __syncthreads();
       for (int i = hi + tid; i < nhi; i += MS_THREADS) {
@@ -230,6 +250,7 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
       }
       __syncthreads();
       bound *= c.fan;
+      blg += flg;
       int kadd = 0;  // exponent added to this level for source `lane`
       if (bound > 0x1p900) {  // per-source maximum of the new level
         double m = 0.0;
@@ -294,11 +315,15 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
         float mv = 1.0f;
         double sv = 1.0;
         if (on) {
-          sv = sc[(size_t)v * 32 + lane];
-          if (FP32) {
-            split_pow2(sv, ev, mv);
-            ev += my_e;
+          if (l < lint) {  // an integer level
+            const long long si = sci[(size_t)v * 32 + lane];
+            sv = i64_to_f64_pos(si);
+            if (FP32) split_pow2_i64(si, ev, mv);
+          } else {
+            sv = sc[(size_t)v * 32 + lane];
+            if (FP32) split_pow2(sv, ev, mv);
           }
+          if (FP32) ev += my_e;
         }
         if (l < Lmax) {
           const int64_t eb = row[v], ee = row[v + 1];
