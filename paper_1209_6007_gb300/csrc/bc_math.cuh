@@ -46,6 +46,16 @@ __device__ __forceinline__ double i64_to_f64_pos(long long x) {
   return __longlong_as_double((long long)(((unsigned long long)(e + 1023) << 52) + (m - (1ull << 52))));
 }
 
+// A double holding a non-negative integer below 2^53, as an integer, from
+// the bit pattern (integer instructions only).
+__device__ __forceinline__ long long f64_to_i64_exact(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  if (e < 0) return 0;  // 0.0
+  const unsigned long long m = (unsigned long long)(b & 0x000fffffffffffffLL) | (1ull << 52);
+  return (long long)(e >= 52 ? m << (e - 52) : m >> (52 - e));
+}
+
 // ceil(log2 x) for x >= 1 from the bit pattern (integer instructions only)
 __device__ __forceinline__ int ceil_log2_pos(double x) {
   const long long b = __double_as_longlong(x);

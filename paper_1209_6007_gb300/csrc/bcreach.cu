@@ -103,12 +103,12 @@ __global__ void k_fill_recip_table() {
 }
 
 // State of one source, in shared (small path) or global (large path) memory.
-template <bool FP32>
+template <bool FP32, typename QT = int32_t>
 struct SrcState {
   int32_t *d;
   double *sig;
   typename CoefT<FP32>::type *coef;  // global path: sigma * ident in phase 1; shared path: == sig
-  int32_t *queue;
+  QT *queue;                         // 16-bit local ids on the shared-memory path
   uint32_t *dmask;     // shared-memory path: DAG successors among the first 32 row entries
   int32_t *lvl_start;  // levels + 2
   int32_t *lvl_exp;    // levels + 1
@@ -117,7 +117,7 @@ struct SrcState {
 };
 constexpr int RED_WS = 15;  // slot of the source weight in SrcState::red
 
-struct Weights {
+struct Weights {  // global-memory path: the int32 arrays; shared path: only the FP64 copies
   const int32_t *reach;   // local, nullable
   const int32_t *ident;   // local, nullable
   const double *init_d;   // reach - 1 as FP64, nullable (converted on the fly)
@@ -151,11 +151,19 @@ struct Debug {
 // vertex also keeps the DAG edges among its first 32 row entries as a bit
 // mask, so phase 2 visits only the successors.  On the shared-memory path
 // the coefficients of phase 2 overwrite the path counts in place.
-template <bool REACH, bool IDENT, bool FP32, bool RESET_BY_QUEUE, typename RowT, typename ColT>
+template <bool REACH, bool IDENT, bool FP32, bool RESET_BY_QUEUE, typename RowT, typename ColT, typename QT>
 __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n, const RowT *__restrict__ row,
-                               const ColT *__restrict__ col, const Weights wt, const SrcState<FP32> st,
+                               const ColT *__restrict__ col, const Weights wt, const SrcState<FP32, QT> st,
                                double *acc, const double fan, int *err, const Debug *dbg,
                                unsigned long long &dag, int *lmax_out = nullptr) {
+  // reach and ident as integers: from the int32 arrays on the global-memory
+  // path, from the FP64 copies (integer instructions) on the shared path
+  auto ident_i = [&](int32_t v) -> long long {
+    return wt.ident ? (long long)wt.ident[v] : f64_to_i64_exact(wt.ident_d[v]);
+  };
+  auto reach_i = [&](int32_t v) -> long long {
+    return wt.reach ? (long long)wt.reach[v] : f64_to_i64_exact(wt.init_d[v]) + 1;
+  };
   int32_t *const d = st.d;
   double *const sig = st.sig;
   long long *const sigi = (long long *)st.sig;
@@ -204,7 +212,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
       const RowT eb = row[v], ee = row[v + 1];
       if (PUSH) {
         // sigma[v] * ident[v], formed by v's own lane (sigma[v] is final)
-        const long long pv = !push ? 0 : (IDENT && v != s ? sigi[v] * (long long)wt.ident[v] : sigi[v]);
+        const long long pv = !push ? 0 : (IDENT && v != s ? sigi[v] * ident_i(v) : sigi[v]);
         uint32_t m = 0u;
         // DISC_CH row entries at a time, so that their shared-memory round
         // trips overlap instead of forming one chain per entry
@@ -253,7 +261,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
       for (int i = lo + g.rank; i < hi; i += g.size) {
         const int32_t v = st.queue[i];
         if (ALIAS) sig[v] = (double)sigi[v];
-        else sk[v] = (double)sigi[v] * (IDENT && v != s ? (double)wt.ident[v] : 1.0);
+        else sk[v] = (double)sigi[v] * (IDENT && v != s ? (double)ident_i(v) : 1.0);
       }
       g.sync();
     }
@@ -303,7 +311,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   // the source's weight reach[s] * ident[s] waits in shared memory: read
   // per vertex, it is never recomputed (FP64) inside the divergent loop
   if (g.rank == 0)
-    st.red[RED_WS] = (double)((REACH ? (long long)wt.reach[s] : 1ll) * (IDENT ? (long long)wt.ident[s] : 1ll));
+    st.red[RED_WS] = (double)((REACH ? reach_i(s) : 1ll) * (IDENT ? ident_i(s) : 1ll));
   g.sync();
   // ---------------------------------------------------------- phase 2
   unsigned long long ndag = 0;
@@ -385,10 +393,10 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
             }
           }
         }
-        const float df = fmaf(mv, sum, REACH ? (float)(wt.reach[v] - 1) : 0.0f);
+        const float df = fmaf(mv, sum, REACH ? (float)(reach_i(v) - 1) : 0.0f);
         dv = (double)df;
         if (l > 0) {
-          const float kv = IDENT ? (float)wt.ident[v] : 1.0f;
+          const float kv = IDENT ? (float)ident_i(v) : 1.0f;
           Coef32 cv;
           cv.c = fmaf(kv, df, kv) / mv;
           cv.e = ev;
@@ -424,11 +432,13 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
 // ---------------------------------------------------------- small path
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// per group: distances, queue and DAG masks (4 bytes each), path counts
-// (later the coefficients, in place) and the group's bc accumulator (8 bytes each)
-__host__ __device__ inline size_t small_group_bytes(int64_t n) {
-  return align16((size_t)n * 4) * 3 + align16((size_t)n * 8) * 2;
+// per group: distances and DAG masks (4 bytes each), the queue (2 bytes),
+// path counts (later the coefficients, in place) and the group's bc
+// accumulator (8 bytes each); the accumulator comes last
+__host__ __device__ inline size_t small_acc_offset(int64_t n) {
+  return align16((size_t)n * 4) * 2 + align16((size_t)n * 2) + align16((size_t)n * 8);
 }
+__host__ __device__ inline size_t small_group_bytes(int64_t n) { return small_acc_offset(n) + align16((size_t)n * 8); }
 
 // bytes of shared memory a component needs with `ng` concurrent sources:
 // the component (rows, 16-bit columns, reach and ident with their FP64 copies) once,
@@ -436,8 +446,8 @@ __host__ __device__ inline size_t small_group_bytes(int64_t n) {
 // and its own bc accumulator
 __host__ __device__ inline size_t small_smem_bytes(int64_t n, int64_t nnz, int ng, bool reach, bool ident) {
   size_t b = align16((size_t)(n + 1) * 4) + align16((size_t)nnz * 2);
-  if (reach) b += align16((size_t)n * 4) + align16((size_t)n * 8);
-  if (ident) b += align16((size_t)n * 4) + align16((size_t)n * 8);
+  if (reach) b += align16((size_t)n * 8);
+  if (ident) b += align16((size_t)n * 8);
   return b + small_group_bytes(n) * (size_t)ng;
 }
 
@@ -469,17 +479,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     p += align16((size_t)(n + 1) * 4);
     uint16_t *col = (uint16_t *)p;  // local ids of a shared-memory piece fit 16 bits
     p += align16((size_t)nnz * 2);
-    int32_t *reach = nullptr, *ident = nullptr;
+    // reach - 1 and ident as FP64 only (integers are read back from them)
     double *init_d = nullptr, *ident_d = nullptr;
     if (REACH) {
-      reach = (int32_t *)p;
-      p += align16((size_t)n * 4);
       init_d = (double *)p;
       p += align16((size_t)n * 8);
     }
     if (IDENT) {
-      ident = (int32_t *)p;
-      p += align16((size_t)n * 4);
       ident_d = (double *)p;
       p += align16((size_t)n * 8);
     }
@@ -488,19 +494,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     for (int v = tid; v <= n; v += SMALL_THREADS) row[v] = (int32_t)(g_row[c.row_off + v] - r0);
     for (int e = tid; e < nnz; e += SMALL_THREADS) col[e] = (uint16_t)g_col[r0 + e];
     for (int v = tid; v < n; v += SMALL_THREADS) {
-      if (REACH) {
-        reach[v] = g_reach[c.vtx_off + v];
-        init_d[v] = (double)(reach[v] - 1);
-      }
-      if (IDENT) {
-        ident[v] = g_ident[c.vtx_off + v];
-        ident_d[v] = (double)ident[v];
-      }
+      if (REACH) init_d[v] = (double)(g_reach[c.vtx_off + v] - 1);
+      if (IDENT) ident_d[v] = (double)g_ident[c.vtx_off + v];
     }
     // zero every group's accumulator
     for (int x = tid; x < ng * n; x += SMALL_THREADS) {
       const int gi = x / n, v = x - gi * n;
-      double *a = (double *)(p + per * gi + align16((size_t)n * 4) * 3 + align16((size_t)n * 8));
+      double *a = (double *)(p + per * gi + small_acc_offset(n));
       a[v] = 0.0;
     }
     __syncthreads();
@@ -511,11 +511,11 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     const bool in_group = gid < ng;
     Group g{tid % gsize, gsize, 1 + gid};
     unsigned char *q = p + per * gid;
-    SrcState<FP32> st;
+    SrcState<FP32, uint16_t> st;
     st.d = (int32_t *)q;
     q += align16((size_t)n * 4);
-    st.queue = (int32_t *)q;
-    q += align16((size_t)n * 4);
+    st.queue = (uint16_t *)q;
+    q += align16((size_t)n * 2);
     st.dmask = (uint32_t *)q;
     q += align16((size_t)n * 4);
     st.sig = (double *)q;
@@ -527,7 +527,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.lvl_exp = lv + lvl_stride;
     st.qtail = &s_qtail[gid];
     st.red = s_red[gid];
-    Weights wt{reach, ident, init_d, ident_d};
+    Weights wt{nullptr, nullptr, init_d, ident_d};
     for (int i = item.s_begin + gid; in_group && i < item.s_end; i += ng) {
       const int32_t s = srcs ? (int32_t)srcs[i] : i;
       bcreach_source<REACH, IDENT, FP32, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr, dag);
@@ -537,7 +537,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     for (int v = tid; v < n; v += SMALL_THREADS) {
       double t = 0.0;
       for (int gi = 0; gi < ng; gi++)
-        t += ((const double *)(p + per * gi + align16((size_t)n * 4) * 3 + align16((size_t)n * 8)))[v];
+        t += ((const double *)(p + per * gi + small_acc_offset(n)))[v];
       if (t != 0.0) atomicAdd(bcp + c.vtx_off + v, t);
     }
     __syncthreads();
