@@ -184,7 +184,7 @@ int bcs_debug_sssp(const bcs_csr *csr, int64_t s, const bcs_opts *opts, int32_t 
  * BCS_EINVAL with a message.  bc_out receives n FP64 values.
  *
  * Memory: the kernels' state lives in one static device array of about
- * 46 MB (64 CTAs x 16,384 vertices), which every GPU that loads this library
+ * 42 MB (64 CTAs x 16,384 vertices), which every GPU that loads this library
  * holds until the process exits.  The first call on a device looks up that
  * array's address (cudaGetSymbolAddress) and may load the library's device
  * code; make that first call before any stream capture.  Every call shares

@@ -145,12 +145,14 @@ struct Debug {
 // before it to FP64 once, and from there on counts are FP64 with a
 // power-of-two exponent per level.  sig holds int64 on the integer levels.
 //
-// One pass over a level's rows both discovers the next level and, on the
-// integer levels, pushes the path counts along the DAG edges it finds
-// (atomics in shared memory, or in L2 on the global-memory path); each
-// vertex also keeps the DAG edges among its first 32 row entries as a bit
-// mask, so phase 2 visits only the successors.  On the shared-memory path
-// the coefficients of phase 2 overwrite the path counts in place.
+// Shared-memory path (!RESET_BY_QUEUE): one pass over a level's rows both
+// discovers the next level and, on the integer levels, pushes the path
+// counts along the DAG edges it finds (shared-memory atomics); each vertex
+// also keeps the DAG edges among its first 32 row entries as a bit mask, so
+// phase 2 visits only the successors; its phase-2 coefficients overwrite the
+// path counts in place.  The global-memory path pulls the counts in a second
+// pass and finds successors by their level (pushing through L2 atomics
+// measured slower on deep graphs, where that path is used).
 template <bool REACH, bool IDENT, bool FP32, bool RESET_BY_QUEUE, typename RowT, typename ColT, typename QT>
 __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n, const RowT *__restrict__ row,
                                const ColT *__restrict__ col, const Weights wt, const SrcState<FP32, QT> st,
@@ -169,13 +171,12 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   long long *const sigi = (long long *)st.sig;
   double *const sk = (double *)st.coef;  // global path: sigma[v] * (v == s ? 1 : ident[v]) in phase 1
   long long *const ski = (long long *)st.coef;
-  constexpr bool PUSH = true;  // both paths push path counts during discovery
+  constexpr bool PUSH = !RESET_BY_QUEUE;
   // Shared-memory path: the coefficient of phase 2 overwrites the path count
   // of the same vertex (st.coef == st.sig); phase 1 keeps sigma alone and
   // multiplies by ident where it reads it.
-  constexpr bool ALIAS = !RESET_BY_QUEUE;
-  // the reciprocal table (filled before any shared-memory launch)
-  constexpr bool TABLE = !RESET_BY_QUEUE;
+  constexpr bool ALIAS = PUSH;
+  long long *const pull_src = IDENT ? ski : sigi;  // sigma * ident (the source counts once)
   if (!RESET_BY_QUEUE) {
     for (int v = g.rank; v < n; v += g.size) {
       d[v] = -1;
@@ -246,6 +247,11 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
           if (e0 - eb < 32) m |= dagb << (int)(e0 - eb);
         }
         st.dmask[v] = m;
+      } else {
+        for (RowT e = eb; e < ee; e++) {
+          const int32_t w = (int32_t)col[e];
+          if (vld(d + w) < 0 && atomicCAS(d + w, -1, L + 1) == -1) st.queue[atomicAdd(st.qtail, 1)] = w;
+        }
       }
     }
     g.sync();
@@ -261,11 +267,25 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
       for (int i = lo + g.rank; i < hi; i += g.size) {
         const int32_t v = st.queue[i];
         if (ALIAS) sig[v] = (double)sigi[v];
-        else sk[v] = (double)sigi[v] * (IDENT && v != s ? (double)ident_i(v) : 1.0);
+        else sk[v] = (double)pull_src[v];
       }
       g.sync();
     }
-    if (!push) {  // an FP64 level: its counts are pulled from level L (one add per DAG edge)
+    if (push) {
+      // the counts of level L+1 are complete
+    } else if (L + 1 < lint) {  // path counts of level L+1, pulled from level L (one add per DAG edge)
+      for (int i = hi + g.rank; i < nhi; i += g.size) {
+        const int32_t w = st.queue[i];
+        long long a = 0;
+        const RowT eb = row[w], ee = row[w + 1];
+        for (RowT e = eb; e < ee; e++) {
+          const int32_t u = (int32_t)col[e];
+          if (d[u] == L) a += pull_src[u];
+        }
+        sigi[w] = a;
+        if (IDENT) ski[w] = a * (long long)wt.ident[w];
+      }
+    } else {
       for (int i = hi + g.rank; i < nhi; i += g.size) {
         const int32_t w = st.queue[i];
         double a = 0.0;
@@ -358,7 +378,7 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
           // correctly rounded reciprocals, so a warp whose lanes all have one
           // issues no FP64 work for it
           double r;
-          if (TABLE && is_int && si < RECIP_TABLE) r = g_recip_table[si];
+          if (PUSH && is_int && si < RECIP_TABLE) r = g_recip_table[si];
           else r = recip_pos(sv);
           ((double *)st.coef)[v] = fma(kv, dv, kv) * r;
         }
@@ -419,12 +439,8 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
     }
     g.sync();
   }
-  if (RESET_BY_QUEUE) {  // distances back to -1 and path counts to 0 for the next source
-    for (int i = g.rank; i < hi; i += g.size) {
-      const int32_t v = st.queue[i];
-      d[v] = -1;
-      sigi[v] = 0;
-    }
+  if (RESET_BY_QUEUE) {
+    for (int i = g.rank; i < hi; i += g.size) d[st.queue[i]] = -1;
     g.sync();
   }
 }
@@ -556,7 +572,6 @@ struct LargeSrc {
 struct LargeScratch {
   int32_t *d;      // -1 between sources
   int32_t *queue;
-  uint32_t *dmask; // DAG successors among a row's first 32 entries
   double *sig;     // 0 between sources
   double *coef;    // 8 bytes per vertex in both precisions
   double *acc;     // 0 between components
@@ -578,7 +593,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
   SrcState<FP32> st;
   st.d = sc.d + b * sc.nmax;
   st.queue = sc.queue + b * sc.nmax;
-  st.dmask = sc.dmask + b * sc.nmax;
+  st.dmask = nullptr;
   st.sig = sc.sig + b * sc.nmax;
   st.coef = (typename CoefT<FP32>::type *)(sc.coef + b * sc.nmax);
   double *acc = sc.acc + b * sc.nmax;
@@ -614,7 +629,7 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
 }
 
 // bytes of global scratch per large-path CTA
-static size_t large_scratch_bytes(int64_t nmax) { return (size_t)nmax * (4 + 4 + 4 + 8 + 8 + 8) + (size_t)(nmax + 2) * 8; }
+static size_t large_scratch_bytes(int64_t nmax) { return (size_t)nmax * (4 + 4 + 8 + 8 + 8) + (size_t)(nmax + 2) * 8; }
 
 // ---------------------------------------------------------- host side
 // The shared-memory kernel's attribute (opt-in shared memory) and its
@@ -980,11 +995,9 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     if ((size_t)grid * per > free_b / 2) grid = std::max<int64_t>(1, (int64_t)(free_b / 2 / per));
     const size_t G = (size_t)grid, NM = (size_t)nmax_large;
     DBuf<int32_t> sd, sq, sls, sle;
-    DBuf<uint32_t> sdm;
     DBuf<double> ssig, scoef, sacc;
     BCS_TRY(sd.alloc(G * NM, ctx.stream));
     BCS_TRY(sq.alloc(G * NM, ctx.stream));
-    BCS_TRY(sdm.alloc(G * NM, ctx.stream));
     BCS_TRY(ssig.alloc(G * NM, ctx.stream));
     BCS_TRY(scoef.alloc(G * NM, ctx.stream));
     BCS_TRY(sacc.alloc(G * NM, ctx.stream));
@@ -993,7 +1006,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     BCS_CUDA(cudaMemsetAsync(sd.p, 0xFF, G * NM * sizeof(int32_t), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(ssig.p, 0, G * NM * sizeof(double), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(sacc.p, 0, G * NM * sizeof(double), ctx.stream));
-    LargeScratch sc{sd.p, sq.p, sdm.p, ssig.p, scoef.p, sacc.p, sls.p, sle.p, (int64_t)NM};
+    LargeScratch sc{sd.p, sq.p, ssig.p, scoef.p, sacc.p, sls.p, sle.p, (int64_t)NM};
     Debug dbgs{po.dbg_d, po.dbg_sig, po.dbg_exp, po.dbg_delta};
     BCS_TRY(BCS_DISPATCH3(launch_large_t, R, I, F, ctx, (int)grid, d_work.p, (int64_t)w.size(), counter.p, d_comps.p,
                           in, sc, d_err.p, dbgs, dbg ? 1 : 0, d_dag.p, d_lmax));
@@ -1087,8 +1100,6 @@ int launch_plain_fixed_scratch(Ctx &ctx, const int64_t *row, const int32_t *col,
   sc.d = (int32_t *)p;
   p += up256(G * N * 4);
   sc.queue = (int32_t *)p;
-  p += up256(G * N * 4);
-  sc.dmask = (uint32_t *)p;
   p += up256(G * N * 4);
   sc.sig = (double *)p;
   p += up256(G * N * 8);

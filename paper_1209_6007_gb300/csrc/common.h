@@ -243,7 +243,7 @@ constexpr size_t FIXED_WORK_ITEM_BYTES = 8;
 constexpr size_t fixed_up256(size_t x) { return (x + 255) & ~(size_t)255; }
 constexpr size_t fixed_scratch_bytes(size_t nmax, size_t ctas) {
   return fixed_up256(nmax * FIXED_WORK_ITEM_BYTES) + 256 /* component */ + 256 /* counter */ + 256 /* err */ +
-         fixed_up256(ctas * nmax * 4) * 3 + fixed_up256(ctas * nmax * 8) * 3 + fixed_up256(ctas * (nmax + 2) * 4) * 2;
+         fixed_up256(ctas * nmax * 4) * 2 + fixed_up256(ctas * nmax * 8) * 3 + fixed_up256(ctas * (nmax + 2) * 4) * 2;
 }
 int launch_plain_fixed_scratch(Ctx &ctx, const int64_t *row, const int32_t *col, int32_t n, double *bc,
                                unsigned char *scratch, int64_t nmax, int ctas, bool fp32);
