@@ -66,6 +66,12 @@ extern "C" {
 #define BCS_STEP_A 2u /* articulation vertices and bridges, Sections 3.2.1-3.2.2 */
 #define BCS_STEP_I 4u /* identical vertices (type I and II), Section 3.3.3 */
 #define BCS_STEPS_ALL 7u
+/* BFS ordering (Section 4.1), opt-in and not part of BCS_STEPS_ALL: the
+ * graph is renumbered in BFS order (one search per connected component, from
+ * its smallest vertex; components kept contiguous), the call runs on the
+ * renumbered graph and bc is mapped back to the caller's ids.  Taken by
+ * bcs_bc_plain, bcs_bc_shattered and bcs_bc_sources. */
+#define BCS_STEP_O 8u
 
 typedef struct bcs_csr {
   int64_t n;              /* number of vertices */

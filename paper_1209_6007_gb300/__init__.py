@@ -21,10 +21,10 @@ from dataclasses import dataclass
 import numpy as np
 
 from ._lib import (NOALLOC_MAX_N, BCS_EINVAL, BCS_ENODEV, BCS_ENOMEM, BCS_EOVERFLOW, BCS_ECUDA, BCS_ETIMEOUT, STEP_A, STEP_D,
-                   STEP_I, STEPS_ALL, ComponentsView, Csr, Opts, Stats, load)
+                   STEP_I, STEP_O, STEPS_ALL, ComponentsView, Csr, Opts, Stats, load)
 
 __all__ = ["bc_plain", "bc_plain_noalloc", "bc_shattered_batch", "NOALLOC_MAX_N", "bc_shattered", "bc_sources", "debug_sssp", "shatter", "last_stats", "BcsError", "load",
-           "STEP_D", "STEP_A", "STEP_I", "STEPS_ALL", "version"]
+           "STEP_D", "STEP_A", "STEP_I", "STEP_O", "STEPS_ALL", "version"]
 
 _NAMES = {BCS_EINVAL: "EINVAL", BCS_ENOMEM: "ENOMEM", BCS_ECUDA: "ECUDA", BCS_ETIMEOUT: "ETIMEOUT",
           BCS_EOVERFLOW: "EOVERFLOW", BCS_ENODEV: "ENODEV"}
@@ -98,25 +98,27 @@ def _csr_of(graph_or_rp, col=None):
     return graph_or_rp, col
 
 
-def bc_plain(row_ptr, col=None, *, delta_fp32: bool = False, stream=None):
-    """Plain Brandes (Algorithm 1) on the whole graph: bc[v] for every v."""
+def bc_plain(row_ptr, col=None, *, delta_fp32: bool = False, stream=None, order: bool = False):
+    """Plain Brandes (Algorithm 1) on the whole graph: bc[v] for every v.
+    order=True renumbers the graph in BFS order first (Section 4.1)."""
     rp, cl = _csr_of(row_ptr, col)
-    a = _Args(rp, cl, delta_fp32=delta_fp32, stream=stream)
+    a = _Args(rp, cl, steps=STEPS_ALL | (STEP_O if order else 0), delta_fp32=delta_fp32, stream=stream)
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_plain(ctypes.byref(a.csr), ctypes.byref(a.opts), ptr))
     return out
 
 
 def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool = False, stream=None,
-                 max_wait: int = 0, autotune: bool = False):
+                 max_wait: int = 0, autotune: bool = False, order: bool = False):
     """Shattered + compressed BC (Section 3), equal to Eq. 1 on the input.
 
     max_wait bounds the polls of device-side waits (0: default, < 0: give up
     at once, which makes the call fail with ETIMEOUT; for tests).  autotune
     times the small-piece work splits once per shape bucket and reuses the
-    fastest."""
+    fastest.  order=True renumbers the graph in BFS order first (Section 4.1)."""
     rp, cl = _csr_of(row_ptr, col)
-    a = _Args(rp, cl, steps=steps, delta_fp32=delta_fp32, stream=stream, max_wait=max_wait, autotune=autotune)
+    a = _Args(rp, cl, steps=steps | (STEP_O if order else 0), delta_fp32=delta_fp32, stream=stream,
+              max_wait=max_wait, autotune=autotune)
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_shattered(ctypes.byref(a.csr), ctypes.byref(a.opts), ptr))
     return out
@@ -154,10 +156,11 @@ def bc_plain_noalloc(row_ptr, col=None, *, delta_fp32: bool = False, stream=None
     return out
 
 
-def bc_sources(row_ptr, col=None, sources=None, *, delta_fp32: bool = False, stream=None):
-    """sum over the given sources s of delta_s(v) (Eq. 2), delta_s(s) = 0."""
+def bc_sources(row_ptr, col=None, sources=None, *, delta_fp32: bool = False, stream=None, order: bool = False):
+    """sum over the given sources s of delta_s(v) (Eq. 2), delta_s(s) = 0.
+    order=True renumbers the graph in BFS order first (Section 4.1)."""
     rp, cl = _csr_of(row_ptr, col)
-    a = _Args(rp, cl, delta_fp32=delta_fp32, stream=stream)
+    a = _Args(rp, cl, steps=STEPS_ALL | (STEP_O if order else 0), delta_fp32=delta_fp32, stream=stream)
     src = np.ascontiguousarray(np.asarray(sources, dtype=np.int64).reshape(-1))
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_sources(ctypes.byref(a.csr), src.ctypes.data if src.size else None, src.size,

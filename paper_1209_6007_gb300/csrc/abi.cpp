@@ -383,6 +383,28 @@ static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double 
   return output_bc(ctx, h, d_bc, bc_out);
 }
 
+// BCS_STEP_O: run `run(renumbered csr, device bc of it, inv)` on the graph
+// renumbered in BFS order, then map bc back to the caller's ids.
+template <class F>
+static int with_bfs_order(Ctx &ctx, const bcs_csr *h, double *bc_out, F &&run) {
+  Input in;
+  BCS_TRY(upload_and_validate(ctx, h, &in));
+  DBuf<int64_t> rp2;
+  DBuf<int32_t> col2, inv;
+  BCS_TRY(bfs_order_graph(ctx, in.g, &rp2, &col2, &inv));
+  bcs_csr h2{h->n, h->nnz, rp2.p, col2.p, 1};
+  DBuf<double> bc2, bcd;
+  BCS_TRY(bc2.alloc(h->n, ctx.stream));
+  BCS_TRY(run(&h2, bc2.p, inv.p));
+  double *d_bc = bc_out;
+  if (!h->on_device) {
+    BCS_TRY(bcd.alloc(h->n, ctx.stream));
+    d_bc = bcd.p;
+  }
+  BCS_TRY(launch_order_map_back(ctx, h->n, inv.p, bc2.p, d_bc));
+  return output_bc(ctx, h, d_bc, bc_out);
+}
+
 }  // namespace bcs
 
 // ================================================================ C ABI
@@ -433,6 +455,10 @@ __attribute__((visibility("default"))) int bcs_bc_plain(const bcs_csr *csr, cons
   return guarded(opts, [&](Ctx &ctx) {
     BcPlanOpts po;
     po.fp32_delta = opts && opts->delta_fp32;
+    if (opts && (opts->steps & BCS_STEP_O))
+      return with_bfs_order(ctx, csr, bc_out, [&](const bcs_csr *h2, double *bc2, const int32_t *) {
+        return plain_impl(ctx, h2, nullptr, 0, bc2, po);
+      });
     return plain_impl(ctx, csr, nullptr, 0, bc_out, po);
   });
 }
@@ -446,11 +472,20 @@ __attribute__((visibility("default"))) int bcs_bc_shattered(const bcs_csr *csr, 
     set_error("bc_out is NULL");
     return BCS_EINVAL;
   }
-  if (opts && (opts->steps & ~BCS_STEPS_ALL)) {
+  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_O))) {
     set_error("unknown bits in opts->steps");
     return BCS_EINVAL;
   }
-  return guarded(opts, [&](Ctx &ctx) { return shattered_impl(ctx, csr, opts, bc_out); });
+  return guarded(opts, [&](Ctx &ctx) {
+    if (opts && (opts->steps & BCS_STEP_O)) {
+      bcs_opts o2 = *opts;
+      o2.steps &= BCS_STEPS_ALL;
+      return with_bfs_order(ctx, csr, bc_out, [&](const bcs_csr *h2, double *bc2, const int32_t *) {
+        return shattered_impl(ctx, h2, &o2, bc2);
+      });
+    }
+    return shattered_impl(ctx, csr, opts, bc_out);
+  });
 }
 
 __attribute__((visibility("default"))) int bcs_bc_shattered_batch(const int64_t *graph_vtx_off, int64_t count,
@@ -515,6 +550,12 @@ __attribute__((visibility("default"))) int bcs_bc_sources(const bcs_csr *csr, co
       }
       return BCS_OK;
     }
+    if (opts && (opts->steps & BCS_STEP_O))
+      return with_bfs_order(ctx, csr, bc_out, [&](const bcs_csr *h2, double *bc2, const int32_t *inv) {
+        std::vector<int64_t> src2;
+        BCS_TRY(map_sources_to_order(ctx, src, k, inv, &src2));
+        return plain_impl(ctx, h2, src2.data(), k, bc2, po);
+      });
     return plain_impl(ctx, csr, src, k, bc_out, po);
   });
 }

@@ -186,6 +186,15 @@ int launch_fill_i64(Ctx &ctx, int64_t *p, int64_t n, int64_t v);
 int launch_add_f64(Ctx &ctx, double *dst, const double *src, int64_t n);
 int launch_exclusive_scan(Ctx &ctx, const int64_t *in, int64_t *out, int64_t n, int64_t *d_total);
 
+// ------------------------------------------------------- BFS ordering
+// Renumber g in BFS order (order.cu): rp2/col2 the renumbered CSR (rows
+// ascending), inv[old id] = new id.
+int bfs_order_graph(Ctx &ctx, const DevGraph &g, DBuf<int64_t> *rp2, DBuf<int32_t> *col2, DBuf<int32_t> *inv);
+// bc[v] = bc2[inv[v]]
+int launch_order_map_back(Ctx &ctx, int64_t n, const int32_t *inv, const double *bc2, double *bc);
+// the new ids of a host list of source ids (host result)
+int map_sources_to_order(Ctx &ctx, const int64_t *src, int64_t k, const int32_t *inv, std::vector<int64_t> *out);
+
 // ------------------------------------------------------- Bc-Reach
 // One component handed to the Bc-Reach kernels.
 struct CompDesc {

@@ -213,6 +213,21 @@ def test_mid_size_piece(gpu):
             assert gpu.last_stats()["n_large_sources"] > 0
 
 
+# ----------------------------------------------------- BFS ordering (4.1)
+@pytest.mark.parametrize("g", [gg.config(1), gg.disjoint_union(gg.config(1), gg.cycle(50), gg.path(2), gg.star(9)),
+                               gg.config(2, scale_pct=3), gg.grid(30, 20)], ids=lambda g: g.name)
+def test_bfs_order_gives_the_same_bc(gpu, g):
+    """Renumbering in BFS order (components contiguous, rows re-sorted) and
+    mapping back leaves every result unchanged up to rounding."""
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_plain(g.row_ptr, g.col, order=True), ref) <= TOL64
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, order=True), ref) <= TOL64
+    rp, col = on_device(g)
+    assert rel(gpu.bc_shattered(rp, col, order=True, delta_fp32=True).cpu().numpy(), ref) <= TOL32
+    src = np.random.default_rng(3).choice(g.n, size=min(40, g.n), replace=False)
+    assert rel(gpu.bc_sources(g.row_ptr, g.col, src, order=True), oracle.bc_sources(g, src)) <= TOL64
+
+
 @pytest.mark.parametrize("cfg", [3, 4], ids=["twins", "road"])
 def test_large_full_size_sources_vs_oracle(gpu, cfg):
     """The twin-heavy (n = 970k) and road-like (n = 2.26M, diameter in the
