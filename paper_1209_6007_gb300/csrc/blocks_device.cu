@@ -34,6 +34,8 @@
 // home copies in ascending vertex id (stable radix sort by block).  Each
 // copy's row is the matching subsequence of the input row, so rows stay in
 // ascending original id.
+#include <cuda/atomic>
+
 #include <algorithm>
 #include <cstdio>
 
@@ -132,9 +134,10 @@ __device__ __forceinline__ int64_t vload64(const int64_t *p) { return *(volatile
 //  2. Subtree sizes nd, reach sums subR and sibling offsets off, bottom-up
 //     without level waits: every leaf starts a walk towards its root and a
 //     vertex is passed on by whichever child completes it last (the
-//     completion counter is bumped after a fence, so the last arriver sees
-//     every sibling's sums).  off[c] is c's place among its siblings, taken
-//     with one atomic on the parent's cursor once nd[c] is final.
+//     completion counter is an acquire-release atomic, so the last arriver
+//     sees every sibling's sums).  off[c] is c's place among its siblings,
+//     taken with one atomic on the parent's cursor once nd[c] is final, and
+//     the parent's size is 1 + its cursor.
 //  3. Preorder pre[v] = pre[parent] + 1 + off[v]: each vertex walks up until
 //     it meets an ancestor whose number is already published, so no vertex
 //     ever waits; subtrees are contiguous ranges [pre, pre + nd).
@@ -203,15 +206,17 @@ __global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__r
   COOP_STRIDE(i, 0, cnt) {  // subtree sizes, reach sums and sibling offsets
     int32_t v = order[i];
     if (nchild[v] != 0) continue;
+    int32_t ndv = 1;  // a leaf
     while (level[v] != 0) {
       const int32_t p = parent[v];
-      const int32_t ndv = uf_vload(nd + v);
       off[v] = atomicAdd(cursor + p, ndv);
-      atomicAdd(nd + p, ndv);
       atomicAdd((unsigned long long *)(subR + p), (unsigned long long)vload64(subR + v));
-      __threadfence();
-      if (atomicAdd(done + p, 1) + 1 != nchild[p]) break;
-      __threadfence();
+      // release: this child's sums are visible to whichever child completes p;
+      // acquire for that last child: it sees every sibling's
+      cuda::atomic_ref<int32_t, cuda::thread_scope_device> dp(done[p]);
+      if (dp.fetch_add(1, cuda::memory_order_acq_rel) + 1 != nchild[p]) break;
+      ndv = 1 + uf_vload(cursor + p);  // p's subtree: itself and its children's
+      nd[p] = ndv;
       v = p;
     }
   }
@@ -256,9 +261,8 @@ __global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__r
       const int32_t p = parent[v];
       atomicMin(low + p, uf_vload(low + v));
       atomicMax(high + p, uf_vload(high + v));
-      __threadfence();
-      if (atomicAdd(done + p, 1) + 1 != nchild[p]) break;
-      __threadfence();
+      cuda::atomic_ref<int32_t, cuda::thread_scope_device> dp(done[p]);
+      if (dp.fetch_add(1, cuda::memory_order_acq_rel) + 1 != nchild[p]) break;
       v = p;
     }
   }
