@@ -240,15 +240,14 @@ __device__ __forceinline__ void push_warp_aggregated(int32_t *queue, unsigned lo
 
 constexpr int PEEL_THREADS = 1024;
 
-// All rounds in one cooperative launch.  cnt[r] is the size of round r's
-// frontier (one counter per round, so no counter is reset while another CTA
-// may still read it); a round decides every removal against the degrees at
-// its start, waits, then applies them.  The arrays the rounds change (deg,
-// reach, alive, bcpre) are plain pointers: no read of them may go through
-// the non-coherent read-only path.  out[0] = rounds run.
+// All rounds in one cooperative launch, one grid-wide wait per round.
+// cnt[r] is the size of round r's frontier (one counter per round, so no
+// counter is reset while another CTA may still read it).  The arrays the
+// rounds change (deg, reach, alive, bcpre) are plain pointers: no read of
+// them may go through the non-coherent read-only path.  out[0] = rounds run.
 __global__ void k_peel_coop(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
                             const int64_t *__restrict__ N, int32_t *deg, int32_t *reach, uint8_t *alive,
-                            int64_t *bcpre, int32_t *fa, int32_t *fb, int32_t *target, unsigned long long *cnt,
+                            int64_t *bcpre, int32_t *fa, int32_t *fb, int32_t *stamp, unsigned long long *cnt,
                             int64_t *out, GridBarrier bar) {
   COOP_STRIDE(v, 0, n) {
     const int32_t d = (int32_t)(rp[v + 1] - rp[v]);
@@ -256,6 +255,7 @@ __global__ void k_peel_coop(int64_t n, const int64_t *__restrict__ rp, const int
     reach[v] = 1;
     alive[v] = 1;
     bcpre[v] = 0;
+    stamp[v] = d == 1 ? 0 : -1;
     if (d == 1) push_warp_aggregated(fa, cnt, (int32_t)v);
   }
   if (!grid_wait(bar)) return;
@@ -264,26 +264,28 @@ __global__ void k_peel_coop(int64_t n, const int64_t *__restrict__ rp, const int
   for (;; r++) {
     const int64_t fcount = (int64_t)*(volatile unsigned long long *)(cnt + r);
     if (fcount == 0) break;
-    COOP_STRIDE(i, 0, fcount) {  // target = the neighbour u is removed into, or -1
-      const int32_t u = cur[i];
-      int32_t t = -1;
-      if (alive[u] && deg[u] == 1) {
-        int32_t v = -1;
-        for (int64_t k = rp[u]; k < rp[u + 1]; k++) {
-          if (alive[col[k]]) {
-            v = col[k];
-            break;
-          }
-        }
-        if (v >= 0 && !(deg[v] == 1 && u < v)) t = v;
-      }
-      target[i] = t;
-    }
-    if (!grid_wait(bar)) return;
+    // Decide and apply in one pass, with the outcome of deciding every
+    // removal against the degrees at the start of the round.  A neighbour is
+    // live iff its degree word is positive (a lone vertex has no
+    // neighbours); stamp[v] is the round whose frontier holds v (each vertex
+    // enters a frontier once, when its degree reaches 1), so a live v with
+    // stamp r was a leaf when the round began.  A leaf u of this round has
+    // one live neighbour v, and only v can change that during the round: if
+    // v is a leaf of this round too, the larger id is removed into the
+    // smaller, and the smaller sees either v's stamp or no live neighbour
+    // left, and stays.  u's reach is final: every other neighbour was
+    // removed into it in earlier rounds.
     COOP_STRIDE(i, 0, fcount) {
-      const int32_t v = target[i];
-      if (v < 0) continue;
       const int32_t u = cur[i];
+      if (uf_vload(deg + u) != 1) continue;
+      int32_t v = -1;
+      for (int64_t k = rp[u]; k < rp[u + 1]; k++) {
+        if (uf_vload(deg + col[k]) > 0) {
+          v = col[k];
+          break;
+        }
+      }
+      if (v < 0 || (uf_vload(stamp + v) == (int32_t)r && u < v)) continue;
       const int64_t ru = reach[u];
       const int64_t nc = N[u];
       atomicAdd((unsigned long long *)(bcpre + u), (unsigned long long)((ru - 1) * (nc - ru)));
@@ -291,7 +293,10 @@ __global__ void k_peel_coop(int64_t n, const int64_t *__restrict__ rp, const int
       atomicAdd(reach + v, (int32_t)ru);
       alive[u] = 0;
       deg[u] = 0;
-      if (atomicSub(deg + v, 1) == 2) push_warp_aggregated(nxt, cnt + r + 1, v);
+      if (atomicSub(deg + v, 1) == 2) {
+        stamp[v] = (int32_t)(r + 1);
+        push_warp_aggregated(nxt, cnt + r + 1, v);
+      }
     }
     if (!grid_wait(bar)) return;
     int32_t *t = cur;
@@ -304,14 +309,14 @@ __global__ void k_peel_coop(int64_t n, const int64_t *__restrict__ rp, const int
 int run_peel(Ctx &ctx, const DevGraph &g, const int64_t *d_N, uint8_t *d_alive, int32_t *d_reach,
              int64_t *d_bcpre) {
   if (g.n == 0) return BCS_OK;
-  DBuf<int32_t> deg, fa, fb, target, err;
+  DBuf<int32_t> deg, fa, fb, stamp, err;
   DBuf<unsigned long long> cnt;
   DBuf<unsigned int> barw;
   DBuf<int64_t> out;
   BCS_TRY(deg.alloc(g.n, ctx.stream));
   BCS_TRY(fa.alloc(g.n, ctx.stream));
   BCS_TRY(fb.alloc(g.n, ctx.stream));
-  BCS_TRY(target.alloc(g.n, ctx.stream));
+  BCS_TRY(stamp.alloc(g.n, ctx.stream));
   BCS_TRY(cnt.alloc(g.n + 2, ctx.stream));  // a round removes at least one vertex: at most n rounds
   BCS_TRY(barw.alloc(2, ctx.stream));
   BCS_TRY(err.alloc(1, ctx.stream));
@@ -330,13 +335,13 @@ int run_peel(Ctx &ctx, const DevGraph &g, const int64_t *d_N, uint8_t *d_alive, 
   int64_t n = g.n;
   const int64_t *rpp = g.rp, *Np = d_N;
   const int32_t *colp = g.col;
-  int32_t *degp = deg.p, *reachp = d_reach, *fap = fa.p, *fbp = fb.p, *tp = target.p;
+  int32_t *degp = deg.p, *reachp = d_reach, *fap = fa.p, *fbp = fb.p, *stp = stamp.p;
   uint8_t *alivep = d_alive;
   int64_t *bcp = d_bcpre, *outp = out.p;
   unsigned long long *cntp = cnt.p;
   void *args[] = {(void *)&n,     (void *)&rpp,   (void *)&colp, (void *)&Np,   (void *)&degp,
                   (void *)&reachp, (void *)&alivep, (void *)&bcp,  (void *)&fap,  (void *)&fbp,
-                  (void *)&tp,    (void *)&cntp,  (void *)&outp, (void *)&gb};
+                  (void *)&stp,   (void *)&cntp,  (void *)&outp, (void *)&gb};
   BCS_CUDA(cudaLaunchCooperativeKernel((const void *)k_peel_coop, dim3(ctx.num_sms), dim3(PEEL_THREADS), args, 0,
                                        ctx.stream));
   ctx.launches++;
