@@ -48,9 +48,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="articulation", choices=["articulation", "batch"],
-                    help="batch: a secondary measurement of many independent graphs in one call "
-                         "(not the headline line)")
+    ap.add_argument("--workload", default="articulation", choices=["articulation", "batch", "side"],
+                    help="batch: a secondary measurement of many independent graphs in one call; "
+                         "side: the articulation workload with added side vertices, shattered with and "
+                         "without the side-vertex step (neither is the headline line)")
     ap.add_argument("--batch-count", type=int, default=20000)
     ap.add_argument("--batch-nmax", type=int, default=4096)
     return ap.parse_args()
@@ -396,12 +397,70 @@ def run_batch(args):
     print(json.dumps(line))
 
 
+def run_side(args):
+    """Side vertices (Section 3.3.2): the articulation workload plus 150,000
+    vertices each joined to both ends of a uniform edge and 50,000 more each
+    joined to an earlier one and its neighbours (every added vertex has a
+    clique for a neighbourhood), shattered with and without the side-vertex
+    step.  Work = n * m of the input; value = with the step."""
+    import torch
+    import graphgen as gg
+    import paper_1209_6007_gb300 as bcs
+    torch.cuda.set_device(0)
+    bcs.load()
+    g = gg.with_side_vertices(gg.config(2, scale_pct=args.scale), 0xB0C00006, 150000 * args.scale // 100,
+                              50000 * args.scale // 100)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res = {}
+    for side in (False, True):
+        for _ in range(args.warmup):
+            bcs.bc_shattered(rp, col, side=side, autotune=True)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        dev_ms, launches, stages = 0.0, 0, {}
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            bcs.bc_shattered(rp, col, side=side, autotune=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            dev_ms += ev0.elapsed_time(ev1)
+            st = bcs.last_stats()
+            launches += int(st["kernel_launches"])
+            for k, v in st.items():
+                if k.startswith("ms_"):
+                    stages[k] = stages.get(k, 0.0) + v / args.steps
+        res[side] = {"ms": dev_ms / args.steps, "launches": launches, "clocks": clocks.stop(), "stages_ms": stages,
+                     "n_side": int(st["n_side"]), "pieces": int(st["n_pieces"]), "n_merged": int(st["n_merged"])}
+    work = float(g.n) * float(g.m)
+    on, off = res[True], res[False]
+    line = {"metric": "BC GTEPS (sources*m / s, n and m of the input graph)",
+            "value": work / (on["ms"] / 1e3) / 1e9, "unit": "GTEPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": on["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "articulation-heavy + side vertices: 5000 ER blocks + 20% chains, then 150,000 "
+                                   "triangle vertices on uniform edges and 50,000 clique-extending vertices",
+                       "n": int(g.n), "m": int(g.m), "l2": "flushed between timed steps (256 MB write)"},
+            "gpu_launches": on["launches"], "clocks": on["clocks"], "side_step": on,
+            "without_side_step": {**off, "gteps": work / (off["ms"] / 1e3) / 1e9},
+            "speedup_of_side_step": off["ms"] / on["ms"],
+            "note": "secondary measurement; the headline line is --workload articulation"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "batch":
         run_batch(args)
+    elif args.workload == "side":
+        run_side(args)
     else:
         run_ours(args)
 

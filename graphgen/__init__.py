@@ -243,6 +243,41 @@ def with_twins_and_pendants(base: Graph, seed: int, n_twins: int, n_pend: int,
     return from_edges(n, sorted(edges), f"{base.name}+tw{n_twins}+ctw{closed_twins}+p{n_pend}")
 
 
+def with_side_vertices(base: Graph, seed: int, n_tri: int, n_grow: int = 0) -> Graph:
+    """Add vertices whose neighbourhoods are cliques: n_tri new vertices, each
+    joined to both ends of a uniform edge of `base`, then n_grow more, each
+    joined to a uniform earlier-added vertex x and to all of x's neighbours
+    (the new vertex's neighbourhood is x's closed one, a clique, and x's
+    stays a clique)."""
+    rng = np.random.default_rng(seed)
+    ed = base.edges()
+    n = base.n
+    nbrs: list[list[int]] = []  # neighbourhoods of the added vertices
+    out = [ed] if ed.size else []
+    if n_tri and ed.shape[0]:
+        pick = ed[rng.integers(0, ed.shape[0], n_tri)]
+        new = np.arange(n, n + n_tri, dtype=np.int64)
+        out += [np.stack([new, pick[:, 0]], 1), np.stack([new, pick[:, 1]], 1)]
+        nbrs = [[int(a), int(b)] for a, b in pick]
+        n += n_tri
+    first = base.n
+    grow = []
+    for _ in range(n_grow if nbrs else 0):
+        k = int(rng.integers(0, len(nbrs)))
+        x = first + k
+        nb = nbrs[k] + [x]
+        grow += [(n, y) for y in nb]
+        for y in nb:
+            if y >= first:
+                nbrs[y - first].append(n)
+        nbrs.append(list(nb))
+        n += 1
+    if grow:
+        out.append(np.asarray(grow, dtype=np.int64))
+    edges = np.concatenate(out) if out else np.zeros((0, 2), dtype=np.int64)
+    return from_edges(n, edges, f"{base.name}+side{n_tri}+grow{n_grow}")
+
+
 def disjoint_union(*graphs: Graph) -> Graph:
     e, off = [], 0
     for g in graphs:

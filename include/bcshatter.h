@@ -72,6 +72,14 @@ extern "C" {
  * renumbered graph and bc is mapped back to the caller's ids.  Taken by
  * bcs_bc_plain, bcs_bc_shattered and bcs_bc_sources. */
 #define BCS_STEP_O 8u
+/* Side vertices (Section 3.3.2, Algorithm 3), opt-in and not part of
+ * BCS_STEPS_ALL: in every merged piece, the vertices whose neighbours are
+ * pairwise adjacent (degree <= 64) leave the piece; each runs one Bc-Reach
+ * search on the full piece with the other vertices counted twice as targets,
+ * the rest run on the piece without them, and two closed-form terms complete
+ * bc'.  The result is the same bc.  Taken by bcs_bc_shattered and
+ * bcs_bc_shattered_batch. */
+#define BCS_STEP_S 16u
 
 typedef struct bcs_csr {
   int64_t n;              /* number of vertices */
@@ -112,6 +120,7 @@ typedef struct bcs_stats {
   int64_t batch_ctas;      /* CTAs of the 32-source launch */
   int64_t small_ng_cap;    /* most sources one small-path CTA ran at once */
   int64_t small_smem_budget; /* shared-memory budget per small-path CTA (bytes) */
+  int64_t n_side;          /* side vertices taken out of the pieces (BCS_STEP_S) */
   double work_nm;          /* sum over pieces of n_c * m_c (m_c undirected) */
   double work_sources_entries; /* sum over processed sources of the piece's CSR entries */
   double work_sources_vertices; /* sum over processed sources of the piece's vertices */
@@ -127,6 +136,7 @@ typedef struct bcs_stats {
   double ms_bcreach_large; /* Bc-Reach, global-memory kernel */
   double ms_mapback;       /* bc accumulation and map back */
   double ms_download;      /* device -> host copy of bc */
+  double ms_side;          /* side-vertex marking and the reduced pieces */
 } bcs_stats;
 
 /*

@@ -17,6 +17,7 @@ BCS_ENODEV = -6
 STEP_D, STEP_A, STEP_I = 1, 2, 4
 STEPS_ALL = 7
 STEP_O = 8  # BFS ordering, opt-in
+STEP_S = 16  # side vertices, opt-in
 NOALLOC_MAX_N = 16384
 
 c_i64, c_i32, c_u32, c_dbl, c_vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double, ctypes.c_void_p
@@ -34,10 +35,10 @@ class Opts(ctypes.Structure):
 class Stats(ctypes.Structure):
     _fields_ = [(name, c_i64) for name in (
         "n_pieces", "n_slots", "n_merged", "n_entries", "peel_rounds", "n_small_items",
-        "n_large_sources", "kernel_launches", "bfs_levels", "dag_edges", "n_ms_batches", "batch_ctas", "small_ng_cap", "small_smem_budget")] + [(name, c_dbl) for name in (
+        "n_large_sources", "kernel_launches", "bfs_levels", "dag_edges", "n_ms_batches", "batch_ctas", "small_ng_cap", "small_smem_budget", "n_side")] + [(name, c_dbl) for name in (
         "work_nm", "work_sources_entries", "work_sources_vertices", "ms_total", "ms_upload", "ms_validate", "ms_cc", "ms_peel",
         "ms_blocks", "ms_ident", "ms_plan", "ms_bcreach_small", "ms_bcreach_large", "ms_mapback",
-        "ms_download")]
+        "ms_download", "ms_side")]
 
 
 class ComponentsView(ctypes.Structure):

@@ -364,7 +364,10 @@ static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double 
   bi.bcp = m.mcorr.p;  // starts with the identical-vertex terms
   BcPlanOpts po;
   po.fp32_delta = o && o->delta_fp32;
-  BCS_TRY(run_bcreach(ctx, S.comps, bi, po));
+  if (steps & BCS_STEP_S)
+    BCS_TRY(run_bcreach_side(ctx, m, S.comps, bi, po, h->n));
+  else
+    BCS_TRY(run_bcreach(ctx, S.comps, bi, po));
   tr.mark("bcreach");
   DBuf<double> bc;
   double *d_bc = bc_out;
@@ -472,14 +475,14 @@ __attribute__((visibility("default"))) int bcs_bc_shattered(const bcs_csr *csr, 
     set_error("bc_out is NULL");
     return BCS_EINVAL;
   }
-  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_O))) {
+  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_O | BCS_STEP_S))) {
     set_error("unknown bits in opts->steps");
     return BCS_EINVAL;
   }
   return guarded(opts, [&](Ctx &ctx) {
     if (opts && (opts->steps & BCS_STEP_O)) {
       bcs_opts o2 = *opts;
-      o2.steps &= BCS_STEPS_ALL;
+      o2.steps &= BCS_STEPS_ALL | BCS_STEP_S;
       return with_bfs_order(ctx, csr, bc_out, [&](const bcs_csr *h2, double *bc2, const int32_t *) {
         return shattered_impl(ctx, h2, &o2, bc2);
       });
@@ -506,7 +509,7 @@ __attribute__((visibility("default"))) int bcs_bc_shattered_batch(const int64_t 
       set_error("graph_vtx_off must be ascending");
       return BCS_EINVAL;
     }
-  if (opts && (opts->steps & ~BCS_STEPS_ALL)) {
+  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_S))) {
     set_error("unknown bits in opts->steps");
     return BCS_EINVAL;
   }

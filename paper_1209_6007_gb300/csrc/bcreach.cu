@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.red = s_red[gid];
     Weights wt{nullptr, nullptr, init_d, ident_d};
     for (int i = item.s_begin + gid; in_group && i < item.s_end; i += ng) {
-      const int32_t s = srcs ? (int32_t)srcs[i] : i;
+      const int32_t s = (srcs && c.src_off >= 0) ? (int32_t)srcs[c.src_off + i] : i;
       bcreach_source<REACH, IDENT, FP32, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr, dag);
     }
     __syncthreads();
@@ -747,15 +747,23 @@ static void remember_split(long long key, int choice) {
   g_tune[key] = choice;
 }
 
-int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po) {
+int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &in, const BcPlanOpts &po) {
   Tracer tr("bcreach", ctx.stream);
   const bool R = in.reach != nullptr, I = in.ident != nullptr, F = po.fp32_delta;
   const bool dbg = po.dbg_d || po.dbg_sig || po.dbg_exp || po.dbg_delta;
-  const int64_t C = (int64_t)comps.size();
-  if (po.sources && C != 1) {
-    set_error("a source list needs exactly one component");
+  const int64_t C = (int64_t)comps_in.size();
+  if (po.sources && (C != 1 || po.srcmap)) {
+    set_error("a source list needs exactly one component and no source map");
     return BCS_EINVAL;
   }
+  // a host source list is the one component's source map (uploaded below)
+  std::vector<CompDesc> comps_src;
+  if (po.sources) {
+    comps_src = comps_in;
+    comps_src[0].src_off = 0;
+    comps_src[0].nsrc = (int32_t)po.nsources;
+  }
+  const std::vector<CompDesc> &comps = po.sources ? comps_src : comps_in;
   std::vector<SmallItem> items;
   std::vector<LargeSrc> work;
   std::vector<int32_t> large, small;
@@ -764,7 +772,8 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   for (int64_t ci = 0; ci < C; ci++) {
     const CompDesc &c = comps[ci];
     if (c.n < 2) continue;
-    const int64_t ns = po.sources ? po.nsources : c.n;
+    const int64_t ns = nsrc_of(c);
+    if (ns == 0) continue;
     work_se += (double)ns * (double)c.nnz;
     work_sv += (double)ns * (double)c.n;
     const bool fits = !po.force_large && !dbg && c.n <= 65535 && small_smem_bytes(c.n, c.nnz, 1, R, I) <= SMALL_SMEM;
@@ -823,7 +832,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     for (size_t k = 0; k < small.size(); k++) {
       const CompDesc &c = comps[small[k]];
       const int ng = ngs[k];
-      const int64_t ns = po.sources ? po.nsources : c.n;
+      const int64_t ns = nsrc_of(c);
       int64_t chunk = (int64_t)std::max(1.0, target / (double)(c.nnz + c.n));
       chunk = ((chunk + ng - 1) / ng) * ng;
       for (int64_t b = 0; b < ns; b += chunk)
@@ -837,8 +846,8 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   // else one source per CTA (more CTAs in flight).
   // BCS_LARGE_PATH=batched|per_source overrides the choice.
   int64_t nbatches = 0;
-  for (int32_t ci : large) nbatches += ((po.sources ? po.nsources : comps[ci].n) + 31) / 32;
-  bool use_ms = !large.empty() && !dbg && !po.per_source_large && nbatches >= 2 * (int64_t)ctx.num_sms;
+  for (int32_t ci : large) nbatches += (nsrc_of(comps[ci]) + 31) / 32;
+  bool use_ms = !large.empty() && !dbg && !po.per_source_large && !po.srcmap && nbatches >= 2 * (int64_t)ctx.num_sms;
   if (use_ms) {
     // its per-CTA scratch grows with the piece: with fewer CTAs than SMs the
     // batches serialise (high-diameter graphs of millions of vertices)
@@ -847,7 +856,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     if (fit < ctx.num_sms) use_ms = false;
   }
   bool forced = false;  // BCS_LARGE_PATH=batched|per_source overrides the choice
-  if (!large.empty() && !dbg && !po.per_source_large) {
+  if (!large.empty() && !dbg && !po.per_source_large && !po.srcmap) {
     if (const char *e = std::getenv("BCS_LARGE_PATH")) {
       if (!std::strcmp(e, "batched")) use_ms = forced = true;
       if (!std::strcmp(e, "per_source")) {
@@ -859,12 +868,29 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   // the one-source-per-CTA list for large pieces, from the `skip`-th source
   // of each piece on (debug output, the depth probe's remainder, or the
   // fallback when a graph is too deep for the 32-source kernel)
+  // the sources of large pieces with a device source map, on the host
+  std::vector<std::vector<int64_t>> large_map(po.srcmap ? large.size() : 0);
+  if (po.srcmap) {
+    for (size_t k = 0; k < large.size(); k++) {
+      const CompDesc &c = comps[large[k]];
+      if (c.src_off < 0) continue;
+      large_map[k].resize(nsrc_of(c));
+      if (!large_map[k].empty())
+        BCS_CUDA(cudaMemcpyAsync(large_map[k].data(), po.srcmap + c.src_off, large_map[k].size() * sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, ctx.stream));
+    }
+    BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  }
+  auto large_src = [&](size_t k, int64_t i) -> int32_t {
+    if (po.sources) return (int32_t)po.sources[i];
+    if (po.srcmap && comps[large[k]].src_off >= 0) return (int32_t)large_map[k][i];
+    return (int32_t)i;
+  };
   auto build_work = [&](int64_t skip) {
     work.clear();
-    for (int32_t ci : large) {
-      const int64_t ns = po.sources ? po.nsources : comps[ci].n;
-      for (int64_t i = skip; i < ns; i++)
-        work.push_back(LargeSrc{ci, (int32_t)(po.sources ? po.sources[i] : i)});
+    for (size_t k = 0; k < large.size(); k++) {
+      const int64_t ns = nsrc_of(comps[large[k]]);
+      for (int64_t i = skip; i < ns; i++) work.push_back(LargeSrc{large[k], large_src(k, i)});
     }
   };
   if (!use_ms) build_work(0);
@@ -890,7 +916,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
   tr.mark("plan0");
   ctx.stats.n_small_items = (int64_t)items.size();
   ctx.stats.n_large_sources = 0;
-  for (int32_t ci : large) ctx.stats.n_large_sources += po.sources ? po.nsources : comps[ci].n;
+  for (int32_t ci : large) ctx.stats.n_large_sources += nsrc_of(comps[ci]);
   ctx.stats.work_sources_entries = work_se;
   ctx.stats.work_sources_vertices = work_sv;
   if (small.empty() && large.empty()) return BCS_OK;
@@ -927,7 +953,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
       BcInput tin = in;
       tin.bcp = target;
       return BCS_DISPATCH3(launch_small_t, R, I, F, ctx, grid, smem, d_items.p, (int)its.size(), d_err.p + 1,
-                           d_comps.p, tin, po.sources ? d_srcs.p : nullptr, lvl.p, lvl_stride, d_err.p, d_dag.p);
+                           d_comps.p, tin, po.sources ? d_srcs.p : po.srcmap, lvl.p, lvl_stride, d_err.p, d_dag.p);
     };
     tr.mark("alloc");
     if (ctx.autotune && tuned == 0) {
@@ -1023,10 +1049,9 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
     const int64_t wave = (int64_t)ctx.num_sms * 3;
     skip = std::max<int64_t>(1, wave / (int64_t)large.size());
     std::vector<LargeSrc> probe;
-    for (int32_t ci : large) {
-      const int64_t ns = po.sources ? po.nsources : comps[ci].n;
-      for (int64_t i = 0; i < std::min(ns, skip); i++)
-        probe.push_back(LargeSrc{ci, (int32_t)(po.sources ? po.sources[i] : i)});
+    for (size_t k = 0; k < large.size(); k++) {
+      const int64_t ns = nsrc_of(comps[large[k]]);
+      for (int64_t i = 0; i < std::min(ns, skip); i++) probe.push_back(LargeSrc{large[k], large_src(k, i)});
     }
     DBuf<int> d_lmax;
     BCS_TRY(d_lmax.alloc(1, ctx.stream));

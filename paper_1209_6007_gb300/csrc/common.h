@@ -205,7 +205,12 @@ struct CompDesc {
   int64_t nnz;      // CSR entries
   double fan;       // bound on sigma growth per level (max over v of sum of
                     // ident over its neighbours)
+  // sources: with a source map, the piece's sources are the local ids
+  // map[src_off .. src_off + nsrc); src_off < 0: every vertex 0..n-1
+  int64_t src_off = -1;
+  int32_t nsrc = -1;  // < 0: n
 };
+__host__ __device__ inline int64_t nsrc_of(const CompDesc &c) { return c.nsrc >= 0 ? c.nsrc : c.n; }
 
 struct BcInput {
   const int64_t *row = nullptr;   // global row offsets (indexed by vertex)
@@ -219,6 +224,9 @@ struct BcPlanOpts {
   bool fp32_delta = false;
   const int64_t *sources = nullptr;  // host; nullable = every vertex
   int64_t nsources = 0;
+  // device source map of the pieces whose src_off >= 0 (local ids, int64);
+  // large pieces then run one source per CTA
+  const int64_t *srcmap = nullptr;
   bool force_large = false;           // route every piece through the global path
   bool per_source_large = false;      // large pieces one source per CTA (no 32-source batches)
   // debug output for a single source (large path only)
@@ -242,6 +250,12 @@ int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32
 // Plan and run Bc-Reach over the given components.  comps are host
 // descriptors; their vertex ranges index BcInput's arrays.
 int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po);
+
+// Bc-Reach over the merged pieces with side vertices taken out (side.cu):
+// the same bc' as run_bcreach(comps, in, po), with in.bcp accumulated.
+// n_graph: vertices of the input graph (a bound on reach).
+int run_bcreach_side(Ctx &ctx, const DevMerged &m, const std::vector<CompDesc> &comps, const BcInput &in,
+                     const BcPlanOpts &po, int64_t n_graph);
 
 }  // namespace bcs
 

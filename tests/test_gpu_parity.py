@@ -309,6 +309,80 @@ def test_batch_rejects_crossing_edges(gpu):
     assert e.value.code == gpu._lib.BCS_EINVAL
 
 
+# ------------------------------------------------- side vertices (3.3.2)
+def side_graphs():
+    out = [gg.complete(7), gg.complete_bipartite(2, 3), gg.disjoint_union(gg.complete(4), gg.complete(5), gg.path(3)),
+           gg.from_edges(4, [(0, 1), (1, 2), (2, 0), (2, 3)])]  # triangle with a pendant
+    for seed in range(4):
+        base = gg.with_side_vertices(gg.gnp(30 + 10 * seed, 0.1, seed), seed, 20 + 5 * seed, 10 * seed)
+        out.append(base)
+        # pendants give the side vertices reach > 1, copies of them ident > 1
+        out.append(gg.with_twins_and_pendants(base, seed, 6, 15, 2))
+    out.append(gg.with_side_vertices(gg.config(1, scale_pct=20), 9, 300, 200))
+    return out
+
+
+SIDE_GRAPHS = side_graphs()
+
+
+def oracle_side_count(g, steps=ALL):
+    """Side vertices of the merged pieces, by definition: a class
+    representative (smallest id) whose merged neighbours in its piece, at
+    most 64 of them, are pairwise adjacent."""
+    count = 0
+    for pc in oracle.shatter(g, steps):
+        drop = {v for c in pc.classes for v in c[1:]}
+        keep = [v for v in pc.vertices if v not in drop]
+        ks = set(keep)
+        adj = {v: {int(w) for w in g.neighbors(v) if int(w) in ks} for v in keep}
+        for v in keep:
+            nb = sorted(adj[v])
+            if 1 <= len(nb) <= 64 and all(b in adj[a] for i, a in enumerate(nb) for b in nb[i + 1:]):
+                count += 1
+    return count
+
+
+@pytest.mark.parametrize("steps", [0, 1, 3, 4, 7])
+@pytest.mark.parametrize("g", SIDE_GRAPHS, ids=lambda g: g.name)
+def test_side_vertices_give_the_same_bc(gpu, g, steps):
+    """Side vertices out of the pieces (Algorithm 3, all of a piece's at
+    once) leave bc unchanged; the count of side vertices is the definition's."""
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, steps=steps, side=True), ref) <= TOL64
+    assert gpu.last_stats()["n_side"] == oracle_side_count(g, steps)
+
+
+def test_side_vertices_fp32_device_and_ordered(gpu):
+    g = SIDE_GRAPHS[-1]
+    ref = oracle.bc(g)
+    rp, col = on_device(g)
+    assert rel(gpu.bc_shattered(rp, col, side=True, delta_fp32=True).cpu().numpy(), ref) <= TOL32
+    assert rel(gpu.bc_shattered(rp, col, side=True, order=True).cpu().numpy(), ref) <= TOL64
+    assert gpu.last_stats()["n_side"] > 100
+
+
+@pytest.mark.parametrize("path", LARGE_PATHS)
+def test_side_vertices_on_a_large_piece(gpu, path, monkeypatch):
+    """A piece too large for shared memory: the side sources run one per
+    CTA from the source map (the 32-source kernel is not used with a map)."""
+    monkeypatch.setenv("BCS_LARGE_PATH", path)
+    g = gg.with_side_vertices(gg.chung_lu(3000, 2.5, 6, 11), 12, 3000, 1500)
+    ref = oracle.bc(g)
+    got = gpu.bc_shattered(g.row_ptr, g.col, side=True)
+    st = gpu.last_stats()
+    assert rel(got, ref) <= TOL64
+    assert st["n_side"] > 2000 and st["n_large_sources"] > 0
+
+
+def test_side_vertices_in_a_batch_and_scaled_articulation(gpu):
+    g, off = gg.batch(40, n_min=16, n_max=1024)
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_shattered_batch(off, g.row_ptr, g.col, side=True), ref) <= TOL64
+    g = gg.config(2, scale_pct=5)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, side=True), oracle.bc(g)) <= TOL64
+    assert gpu.last_stats()["n_side"] > 0
+
+
 # --------------------------------------------------------------- errors
 def test_malformed_inputs_rejected(gpu):
     bad = {
