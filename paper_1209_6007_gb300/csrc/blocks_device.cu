@@ -82,26 +82,33 @@ __global__ void k_alive_deg(int64_t n, const int64_t *__restrict__ rp, const int
   }
 }
 
-// root of each component's tree: its smallest live vertex with a live edge
-// (lanes of a warp with the same label combine first: a giant component
-// would otherwise send one atomic per vertex to a single address)
+// root of each component's tree: its live vertex of largest live degree,
+// the smallest id among those (a hub tends to sit near the middle of the
+// graph, so the BFS has fewer levels than from an arbitrary vertex; any root
+// is correct).  key = degree * 2^32 + (2^31 - 1 - id), maximised; lanes of
+// a warp with the same label combine first: a giant component would
+// otherwise send one atomic per vertex to a single address.
 __global__ void k_roots(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ label,
-                        int32_t *root_of) {
+                        unsigned long long *root_key) {
   GRID_STRIDE(v, n) {
-    if (adeg[v] > 0) {
+    const int32_t dv = adeg[v];
+    if (dv > 0) {
       const int32_t l = label[v];
       const unsigned m = __match_any_sync(__activemask(), l);
-      const int32_t lo = __reduce_min_sync(m, (int32_t)v);
-      if ((int)(threadIdx.x & 31) == __ffs(m) - 1) atomicMin(root_of + l, lo);
+      const unsigned dmax = __reduce_max_sync(m, (unsigned)dv);
+      const unsigned lo = __reduce_min_sync(m, (unsigned)dv == dmax ? (unsigned)v : 0xffffffffu);
+      if ((int)(threadIdx.x & 31) == __ffs(m) - 1)
+        atomicMax(root_key + l, ((unsigned long long)dmax << 32) | (unsigned long long)(0x7fffffffu - lo));
     }
   }
 }
 
 __global__ void k_bfs_init(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ label,
-                           const int32_t *__restrict__ root_of, int32_t *level, int32_t *parent, int32_t *order,
-                           unsigned long long *tail) {
+                           const unsigned long long *__restrict__ root_key, int32_t *level, int32_t *parent,
+                           int32_t *order, unsigned long long *tail) {
   GRID_STRIDE(v, n) {
-    const bool root = adeg[v] > 0 && root_of[label[v]] == (int32_t)v;
+    const bool root =
+        adeg[v] > 0 && (int64_t)(0x7fffffffu - (unsigned)(root_key[label[v]] & 0xffffffffull)) == v;
     parent[v] = root ? -1 : INT32_MAX;  // the BFS takes the minimum over the level above
     level[v] = root ? 0 : -1;
     if (root) push_aggr(order, tail, (int32_t)v);
@@ -465,7 +472,8 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
   const int B = 256;
   const int gv = gridv(n, B, ctx.num_sms * 32);
   Tracer tr("pieces", ctx.stream);
-  DBuf<int32_t> adeg, level, parent, order, bid, home_slot, pre, nd, low, high, uf, blk, root_of, top, top_slot;
+  DBuf<int32_t> adeg, level, parent, order, bid, home_slot, pre, nd, low, high, uf, blk, top, top_slot;
+  DBuf<unsigned long long> root_key;
   DBuf<int64_t> subR, side, childblk, flag, fscan, bcnt, boff, tot, hflag, hpos;
   BCS_TRY(adeg.alloc(n, ctx.stream));
   BCS_TRY(level.alloc(n, ctx.stream));
@@ -485,12 +493,12 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
   int64_t tree_cnt = 0;     // vertices in the forest (art) / with a slot
   std::vector<int64_t> lvl_off;
   if (art) {
-    BCS_TRY(root_of.alloc(n, ctx.stream));
+    BCS_TRY(root_key.alloc(n, ctx.stream));
     BCS_TRY(order.alloc(n, ctx.stream));
-    BCS_CUDA(cudaMemsetAsync(root_of.p, 0x7f, n * sizeof(int32_t), ctx.stream));
+    BCS_CUDA(cudaMemsetAsync(root_key.p, 0, n * sizeof(unsigned long long), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(tot.p, 0, 2 * sizeof(int64_t), ctx.stream));
-    k_roots<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, root_of.p);
-    k_bfs_init<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, root_of.p, level.p, parent.p, order.p,
+    k_roots<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, root_key.p);
+    k_bfs_init<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, root_key.p, level.p, parent.p, order.p,
                                          (unsigned long long *)tot.p);
     ctx.launches += 2;
     BCS_CUDA(cudaGetLastError());

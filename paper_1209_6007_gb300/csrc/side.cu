@@ -60,12 +60,15 @@ __device__ __forceinline__ int64_t piece_of(const int64_t *__restrict__ piece_of
   return lo;
 }
 
-// x among col[a..b) (a row in ascending order; an unsorted row can only
-// hide a side vertex, never invent one)
-__device__ __forceinline__ bool row_has(const int32_t *__restrict__ col, int64_t a, int64_t b, int32_t x) {
+// whether the row col[a..b) of a piece holds the vertex of original id x:
+// rows are in ascending original id (local ids put a block's top vertex
+// first, so they are not), org[base + local id] = original id.  A row out
+// of that order could only hide a side vertex, never invent one.
+__device__ __forceinline__ bool row_has(const int32_t *__restrict__ col, const int32_t *__restrict__ org,
+                                        int64_t base, int64_t a, int64_t b, int32_t x) {
   while (a < b) {
     const int64_t mid = (a + b) >> 1;
-    const int32_t c = col[mid];
+    const int32_t c = org[base + col[mid]];
     if (c == x) return true;
     if (c < x)
       a = mid + 1;
@@ -75,11 +78,12 @@ __device__ __forceinline__ bool row_has(const int32_t *__restrict__ col, int64_t
   return false;
 }
 
-// side[v] = 1 if v's merged neighbours are pairwise adjacent; nside[p]
-// counts them per piece
+// side[v] = 1 if v's merged neighbours are pairwise adjacent (binary
+// searches by original id); nside[p]
+// counts them per piece; vpiece[v] = v's piece
 __global__ void k_side_mark(int64_t M, const int64_t *__restrict__ piece_off, int64_t P,
-                            const int64_t *__restrict__ mrow, const int32_t *__restrict__ mcol, int64_t *side,
-                            int32_t *nside) {
+                            const int64_t *__restrict__ mrow, const int32_t *__restrict__ mcol,
+                            const int32_t *__restrict__ morg, int32_t *vpiece, uint8_t *side, int32_t *nside) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (int64_t)gridDim.x * blockDim.x) {
     const int64_t p = piece_of(piece_off, P, v);
     const int64_t base = piece_off[p];
@@ -89,56 +93,61 @@ __global__ void k_side_mark(int64_t M, const int64_t *__restrict__ piece_off, in
       const int64_t a = base + mcol[i];
       const int64_t a0 = mrow[a], a1 = mrow[a + 1];
       for (int64_t j = i + 1; j < r1; j++)
-        if (!row_has(mcol, a0, a1, mcol[j])) {
+        if (!row_has(mcol, morg, base, a0, a1, morg[base + mcol[j]])) {
           s = false;
           break;
         }
     }
+    vpiece[v] = (int32_t)p;
     side[v] = s;
     if (s) atomicAdd(nside + p, 1);
   }
 }
 
-// reach2 (targets outside S doubled in pieces that have side vertices),
-// red[v] = v belongs to a reduced piece, and the per-piece sums SW / NW of
-// reach * ident over S and outside it
-__global__ void k_side_prep(int64_t M, const int64_t *__restrict__ piece_off, int64_t P,
-                            const int64_t *__restrict__ side, const int32_t *__restrict__ nside,
-                            const int32_t *__restrict__ reach, const int32_t *__restrict__ ident, int32_t *reach2,
-                            int64_t *red, unsigned long long *sw, unsigned long long *nw) {
+// reach2 (targets outside S doubled in pieces that have side vertices), the
+// scan input side[v] + 2^32 red[v] (red: v belongs to a reduced piece), and
+// the per-piece sums SW / NW of reach * ident over S and outside it
+__global__ void k_side_prep(int64_t M, const int32_t *__restrict__ vpiece, const uint8_t *__restrict__ side,
+                            const int32_t *__restrict__ nside, const int32_t *__restrict__ reach,
+                            const int32_t *__restrict__ ident, int32_t *reach2, int64_t *flags,
+                            unsigned long long *sw, unsigned long long *nw) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = piece_of(piece_off, P, v);
+    const int32_t p = vpiece[v];
     const bool has = nside[p] > 0, sv = side[v] != 0;
     const int32_t r = reach ? reach[v] : 1;
     const int32_t k = ident ? ident[v] : 1;
     reach2[v] = (has && !sv) ? 2 * r : r;
-    red[v] = has && !sv;
+    flags[v] = (int64_t)sv | ((int64_t)(has && !sv) << 32);
     if (has) atomicAdd(sv ? sw + p : nw + p, (unsigned long long)((int64_t)r * k));
   }
 }
 
+// low and high halves of the packed scan: side vertices / reduced vertices
+// before v
+__device__ __forceinline__ int64_t side_before(int64_t x) { return x & 0xffffffffll; }
+__device__ __forceinline__ int64_t red_before(int64_t x) { return x >> 32; }
+
 // The side-source map, the reduced pieces' degrees, weights and ids, and
-// the closed-form terms.  sscan / rid: exclusive scans of side / red.
-__global__ void k_side_lists(int64_t M, const int64_t *__restrict__ piece_off, int64_t P,
+// the closed-form terms.
+__global__ void k_side_lists(int64_t M, const int32_t *__restrict__ vpiece, const int64_t *__restrict__ piece_off,
                              const int64_t *__restrict__ mrow, const int32_t *__restrict__ mcol,
-                             const int64_t *__restrict__ side, const int64_t *__restrict__ sscan,
-                             const int64_t *__restrict__ rid, const int32_t *__restrict__ nside,
-                             const int32_t *__restrict__ reach, const int32_t *__restrict__ ident,
-                             const unsigned long long *__restrict__ sw, const unsigned long long *__restrict__ nw,
-                             int64_t *srcmap, int64_t *rdeg, int32_t *rreach, int32_t *rident, int32_t *rmap,
-                             unsigned long long *rnnz, double *bcp) {
+                             const uint8_t *__restrict__ side, const int64_t *__restrict__ scan,
+                             const int32_t *__restrict__ nside, const int32_t *__restrict__ reach,
+                             const int32_t *__restrict__ ident, const unsigned long long *__restrict__ sw,
+                             const unsigned long long *__restrict__ nw, int64_t *srcmap, int64_t *rdeg,
+                             int32_t *rreach, int32_t *rident, int32_t *rmap, unsigned long long *rnnz, double *bcp) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t p = piece_of(piece_off, P, v);
+    const int32_t p = vpiece[v];
     if (nside[p] == 0) continue;
     const int64_t base = piece_off[p];
     const int64_t r = reach ? reach[v] : 1;
     if (side[v]) {
-      srcmap[base + (sscan[v] - sscan[base])] = v - base;
+      srcmap[base + (side_before(scan[v]) - side_before(scan[base]))] = v - base;
       bcp[v] += (double)((r - 1) * (int64_t)nw[p]);
       continue;
     }
     bcp[v] -= (double)(r * (int64_t)sw[p]);
-    const int64_t x = rid[v];
+    const int64_t x = red_before(scan[v]);
     int64_t d = 0;
     for (int64_t i = mrow[v]; i < mrow[v + 1]; i++) d += side[base + mcol[i]] == 0;
     rdeg[x] = d;
@@ -151,19 +160,18 @@ __global__ void k_side_lists(int64_t M, const int64_t *__restrict__ piece_off, i
 
 // the reduced CSR: each row keeps its neighbours outside S, renumbered
 // inside the reduced piece (ascending order is kept)
-__global__ void k_side_fill(int64_t M, const int64_t *__restrict__ piece_off, int64_t P,
+__global__ void k_side_fill(int64_t M, const int32_t *__restrict__ vpiece, const int64_t *__restrict__ piece_off,
                             const int64_t *__restrict__ mrow, const int32_t *__restrict__ mcol,
-                            const int64_t *__restrict__ side, const int64_t *__restrict__ red,
-                            const int64_t *__restrict__ rid, const int64_t *__restrict__ rrow, int32_t *rcol) {
+                            const uint8_t *__restrict__ side, const int64_t *__restrict__ flags,
+                            const int64_t *__restrict__ scan, const int64_t *__restrict__ rrow, int32_t *rcol) {
   for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < M; v += (int64_t)gridDim.x * blockDim.x) {
-    if (!red[v]) continue;
-    const int64_t p = piece_of(piece_off, P, v);
-    const int64_t base = piece_off[p];
-    const int64_t rbase = rid[base];
-    int64_t pos = rrow[rid[v]];
+    if (red_before(flags[v]) == 0) continue;
+    const int64_t base = piece_off[vpiece[v]];
+    const int64_t rbase = red_before(scan[base]);
+    int64_t pos = rrow[red_before(scan[v])];
     for (int64_t i = mrow[v]; i < mrow[v + 1]; i++) {
       const int64_t w = base + mcol[i];
-      if (!side[w]) rcol[pos++] = (int32_t)(rid[w] - rbase);
+      if (!side[w]) rcol[pos++] = (int32_t)(red_before(scan[w]) - rbase);
     }
   }
 }
@@ -178,7 +186,7 @@ __global__ void k_side_scatter(int64_t nred, const int32_t *__restrict__ rmap, c
 
 int run_bcreach_side(Ctx &ctx, const DevMerged &m, const std::vector<CompDesc> &comps, const BcInput &in,
                      const BcPlanOpts &po, int64_t n_graph) {
-  const int64_t M = m.nmerged, P = m.npieces;
+  const int64_t M = m.nmerged, P = m.npieces, E = m.nentries;
   // reach <= n_graph, and the doubled target weights must stay in int32
   if (M == 0 || P == 0 || n_graph >= ((int64_t)1 << 30)) return run_bcreach(ctx, comps, in, po);
   Tracer tr("side", ctx.stream);
@@ -186,68 +194,63 @@ int run_bcreach_side(Ctx &ctx, const DevMerged &m, const std::vector<CompDesc> &
   tm.start();
   const int maxb = ctx.num_sms * 16;
   const int gm = grid_of(M, maxb);
-  DBuf<int64_t> side, sscan, red, rid, totals;
-  DBuf<int32_t> nside, reach2;
+  // every array sized for the worst case (no piece loses a vertex), so the
+  // step needs one host synchronisation, for the descriptors
+  DBuf<uint8_t> side;
+  DBuf<int32_t> vpiece, nside, reach2, rreach, rident, rmap, rcol;
+  DBuf<int64_t> flags, scan, srcmap, rdeg, rrow, totals;
   DBuf<unsigned long long> sums;  // sw[P], nw[P], rnnz[P]
   BCS_TRY(side.alloc(M, ctx.stream));
-  BCS_TRY(sscan.alloc(M, ctx.stream));
-  BCS_TRY(red.alloc(M, ctx.stream));
-  BCS_TRY(rid.alloc(M, ctx.stream));
-  BCS_TRY(totals.alloc(2, ctx.stream));
+  BCS_TRY(vpiece.alloc(M, ctx.stream));
   BCS_TRY(nside.alloc(P, ctx.stream));
   BCS_TRY(reach2.alloc(M, ctx.stream));
+  BCS_TRY(flags.alloc(M, ctx.stream));
+  BCS_TRY(scan.alloc(M, ctx.stream));
+  BCS_TRY(srcmap.alloc(M, ctx.stream));
+  BCS_TRY(rdeg.alloc(M, ctx.stream));
+  BCS_TRY(rrow.alloc(M + 1, ctx.stream));
+  BCS_TRY(rreach.alloc(M, ctx.stream));
+  if (in.ident) BCS_TRY(rident.alloc(M, ctx.stream));
+  BCS_TRY(rmap.alloc(M, ctx.stream));
+  BCS_TRY(rcol.alloc(std::max<int64_t>(E, 1), ctx.stream));
+  BCS_TRY(totals.alloc(1, ctx.stream));
   BCS_TRY(sums.alloc(3 * P, ctx.stream));
   BCS_CUDA(cudaMemsetAsync(nside.p, 0, P * sizeof(int32_t), ctx.stream));
   BCS_CUDA(cudaMemsetAsync(sums.p, 0, 3 * P * sizeof(unsigned long long), ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(rdeg.p, 0, M * sizeof(int64_t), ctx.stream));
   unsigned long long *sw = sums.p, *nw = sums.p + P, *rnnz = sums.p + 2 * P;
-  k_side_mark<<<gm, SIDE_BLOCK, 0, ctx.stream>>>(M, m.piece_off.p, P, m.mrow.p, m.mcol.p, side.p, nside.p);
-  k_side_prep<<<gm, SIDE_BLOCK, 0, ctx.stream>>>(M, m.piece_off.p, P, side.p, nside.p, in.reach, in.ident,
-                                                 reach2.p, red.p, sw, nw);
+  k_side_mark<<<gm, SIDE_BLOCK, 0, ctx.stream>>>(M, m.piece_off.p, P, m.mrow.p, m.mcol.p, m.morg.p, vpiece.p,
+                                                 side.p, nside.p);
+  k_side_prep<<<gm, SIDE_BLOCK, 0, ctx.stream>>>(M, vpiece.p, side.p, nside.p, in.reach, in.ident, reach2.p,
+                                                 flags.p, sw, nw);
   ctx.launches += 2;
   BCS_CUDA(cudaGetLastError());
-  BCS_TRY(launch_exclusive_scan(ctx, side.p, sscan.p, M, totals.p));
-  BCS_TRY(launch_exclusive_scan(ctx, red.p, rid.p, M, totals.p + 1));
-  std::vector<int32_t> h_nside(P);
-  int64_t h_tot[2] = {0, 0};
-  BCS_CUDA(cudaMemcpyAsync(h_nside.data(), nside.p, P * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
-  BCS_CUDA(cudaMemcpyAsync(h_tot, totals.p, 2 * sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
-  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
-  const int64_t nside_total = h_tot[0], nred = h_tot[1];
-  ctx.stats.n_side = nside_total;
-  tr.mark("mark");
-  if (nside_total == 0) {
-    ctx.stats.ms_side = tm.stop_ms();
-    return run_bcreach(ctx, comps, in, po);
-  }
-  DBuf<int64_t> srcmap, rdeg, rrow;
-  DBuf<int32_t> rreach, rident, rmap, rcol;
-  DBuf<double> bred;
-  BCS_TRY(srcmap.alloc(M, ctx.stream));
-  BCS_TRY(rdeg.alloc(nred, ctx.stream));
-  BCS_TRY(rrow.alloc(nred + 1, ctx.stream));
-  BCS_TRY(rreach.alloc(nred, ctx.stream));
-  if (in.ident) BCS_TRY(rident.alloc(nred, ctx.stream));
-  BCS_TRY(rmap.alloc(nred, ctx.stream));
-  k_side_lists<<<gm, SIDE_BLOCK, 0, ctx.stream>>>(M, m.piece_off.p, P, m.mrow.p, m.mcol.p, side.p, sscan.p, rid.p,
+  BCS_TRY(launch_exclusive_scan(ctx, flags.p, scan.p, M, totals.p));
+  k_side_lists<<<gm, SIDE_BLOCK, 0, ctx.stream>>>(M, vpiece.p, m.piece_off.p, m.mrow.p, m.mcol.p, side.p, scan.p,
                                                   nside.p, in.reach, in.ident, sw, nw, srcmap.p, rdeg.p, rreach.p,
                                                   in.ident ? rident.p : nullptr, rmap.p, rnnz, in.bcp);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
-  int64_t rtot = 0;
-  if (nred > 0) {
-    BCS_TRY(launch_exclusive_scan(ctx, rdeg.p, rrow.p, nred, rrow.p + nred));
-    BCS_CUDA(cudaMemcpyAsync(&rtot, rrow.p + nred, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
-  }
+  BCS_TRY(launch_exclusive_scan(ctx, rdeg.p, rrow.p, M, rrow.p + M));
+  k_side_fill<<<gm, SIDE_BLOCK, 0, ctx.stream>>>(M, vpiece.p, m.piece_off.p, m.mrow.p, m.mcol.p, side.p, flags.p,
+                                                 scan.p, rrow.p, rcol.p);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  std::vector<int32_t> h_nside(P);
   std::vector<unsigned long long> h_rnnz(P);
+  int64_t h_tot = 0;
+  BCS_CUDA(cudaMemcpyAsync(h_nside.data(), nside.p, P * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
   BCS_CUDA(cudaMemcpyAsync(h_rnnz.data(), rnnz, P * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaMemcpyAsync(&h_tot, totals.p, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
   BCS_CUDA(cudaStreamSynchronize(ctx.stream));
-  BCS_TRY(rcol.alloc(std::max<int64_t>(rtot, 1), ctx.stream));
-  if (nred > 0) {
-    k_side_fill<<<gm, SIDE_BLOCK, 0, ctx.stream>>>(M, m.piece_off.p, P, m.mrow.p, m.mcol.p, side.p, red.p, rid.p,
-                                                   rrow.p, rcol.p);
-    ctx.launches++;
-    BCS_CUDA(cudaGetLastError());
+  const int64_t nside_total = h_tot & 0xffffffffll, nred = h_tot >> 32;
+  ctx.stats.n_side = nside_total;
+  tr.mark("mark+reduce");
+  if (nside_total == 0) {
+    ctx.stats.ms_side = tm.stop_ms();
+    return run_bcreach(ctx, comps, in, po);
   }
+  DBuf<double> bred;
   BCS_TRY(bred.alloc(std::max<int64_t>(nred, 1), ctx.stream));
   BCS_CUDA(cudaMemsetAsync(bred.p, 0, std::max<int64_t>(nred, 1) * sizeof(double), ctx.stream));
   // descriptors: the side pass over every piece (its side vertices as the
@@ -274,7 +277,6 @@ int run_bcreach_side(Ctx &ctx, const DevMerged &m, const std::vector<CompDesc> &
     roff += nr;
   }
   ctx.stats.ms_side = tm.stop_ms();
-  tr.mark("reduce");
   BcInput a = in;
   a.reach = reach2.p;
   BcPlanOpts pa = po;
