@@ -147,8 +147,9 @@ int bcs_bc_plain(const bcs_csr *csr, const bcs_opts *opts, double *bc_out);
 
 /*
  * Shattered and compressed BC (Section 3): the steps in opts->steps are
- * applied once in the order D, A, I; Bc-Reach (Algorithm 2, with the
- * identical-vertex terms of Section 3.3.3) runs on every piece; the piece
+ * applied once in the order D, A, I (then S, if set, on the merged pieces);
+ * Bc-Reach (Algorithm 2, with the identical-vertex terms of Section 3.3.3,
+ * and Algorithm 3's searches for side vertices) runs on every piece; the piece
  * scores are mapped back with Eq. 5 (bc[v] = sum over copies v' of v of
  * bc'[v']) plus the closed-form terms of the removed vertices.  The result
  * equals Eq. 1 on the input graph (Theorem 1 and its corollaries).
