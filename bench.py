@@ -48,10 +48,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="articulation", choices=["articulation", "batch", "side"],
+    ap.add_argument("--workload", default="articulation", choices=["articulation", "batch", "side", "unequal"],
                     help="batch: a secondary measurement of many independent graphs in one call; "
                          "side: the articulation workload with added side vertices, shattered with and "
-                         "without the side-vertex step (neither is the headline line)")
+                         "without the side-vertex step; unequal: a twin-heavy graph whose twins carry "
+                         "pendants, with and without merging twins of unequal reach (none is the headline line)")
     ap.add_argument("--batch-count", type=int, default=20000)
     ap.add_argument("--batch-nmax", type=int, default=4096)
     return ap.parse_args()
@@ -453,6 +454,65 @@ def run_side(args):
     print(json.dumps(line))
 
 
+def run_unequal(args):
+    """Identical vertices of unequal reach: a Chung-Lu core (25,000 vertices,
+    gamma 2.1, mean degree 12; the twin workload's core at 5 %) plus 7,500
+    open twins (copies of a uniform core vertex's neighbour set) and 17,500
+    pendants on uniform vertices, twins included, so that twins differ in
+    reach.  Shattered with equal-reach classes and with classes of any reach;
+    work = n * m of the input; value = with unequal-reach classes."""
+    import torch
+    import graphgen as gg
+    import paper_1209_6007_gb300 as bcs
+    torch.cuda.set_device(0)
+    bcs.load()
+    g = gg.with_twins_and_pendants(gg.chung_lu(25000, 2.1, 12, 0xB0C00007), 0xB0C00007, 7500, 17500)
+    rp = torch.from_numpy(g.row_ptr).cuda()
+    col = torch.from_numpy(g.col).cuda()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+    res, out = {}, {}
+    for unequal in (False, True):
+        for _ in range(args.warmup):
+            bcs.bc_shattered(rp, col, unequal=unequal, autotune=True)
+        torch.cuda.synchronize()
+        clocks = ClockSampler(0)
+        clocks.start()
+        dev_ms, launches, stages = 0.0, 0, {}
+        for _ in range(args.steps):
+            flush.zero_()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            bc = bcs.bc_shattered(rp, col, unequal=unequal, autotune=True)
+            ev1.record(stream)
+            ev1.synchronize()
+            dev_ms += ev0.elapsed_time(ev1)
+            st = bcs.last_stats()
+            launches += int(st["kernel_launches"])
+            for k, v in st.items():
+                if k.startswith("ms_"):
+                    stages[k] = stages.get(k, 0.0) + v / args.steps
+        out[unequal] = bc
+        res[unequal] = {"ms": dev_ms / args.steps, "launches": launches, "clocks": clocks.stop(), "stages_ms": stages,
+                        "n_merged": int(st["n_merged"]), "pieces": int(st["n_pieces"]),
+                        "large_sources": int(st["n_large_sources"])}
+    work = float(g.n) * float(g.m)
+    on, off = res[True], res[False]
+    diff = float((out[True] - out[False]).abs().max() / out[False].abs().max().clamp(min=1.0))
+    line = {"metric": "BC GTEPS (sources*m / s, n and m of the input graph)",
+            "value": work / (on["ms"] / 1e3) / 1e9, "unit": "GTEPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": on["ms"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "twins of unequal reach: Chung-Lu core 25,000 (gamma 2.1, mean degree 12) + 7,500 "
+                                   "open twins + 17,500 pendants on uniform vertices", "n": int(g.n), "m": int(g.m),
+                       "l2": "flushed between timed steps (256 MB write)"},
+            "gpu_launches": on["launches"], "clocks": on["clocks"], "unequal_reach_classes": on,
+            "equal_reach_classes": {**off, "gteps": work / (off["ms"] / 1e3) / 1e9},
+            "speedup_of_unequal_classes": off["ms"] / on["ms"], "max_rel_diff_between_the_two": diff,
+            "note": "secondary measurement; the headline line is --workload articulation"}
+    print(json.dumps(line))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -461,6 +521,8 @@ def main():
         run_batch(args)
     elif args.workload == "side":
         run_side(args)
+    elif args.workload == "unequal":
+        run_unequal(args)
     else:
         run_ours(args)
 

@@ -80,6 +80,15 @@ extern "C" {
  * bc'.  The result is the same bc.  Taken by bcs_bc_shattered and
  * bcs_bc_shattered_batch. */
 #define BCS_STEP_S 16u
+/* Identical vertices of unequal reach (the reading of Section 3.3.3 where
+ * reach and ident meet), opt-in and not part of BCS_STEPS_ALL: with
+ * BCS_STEP_I, classes are keyed on the neighbourhood alone; a class of K
+ * members with reaches r_i becomes one vertex whose dependency starts at
+ * (sum r_i) / K - 1 and whose source weight is sum r_i, and each member's own
+ * terms are added to its copy in closed form.  The result is the same bc.
+ * Taken by bcs_bc_shattered and bcs_bc_shattered_batch; not combinable with
+ * BCS_STEP_S (BCS_EINVAL). */
+#define BCS_STEP_U 32u
 
 typedef struct bcs_csr {
   int64_t n;              /* number of vertices */

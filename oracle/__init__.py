@@ -20,7 +20,8 @@ Functions and the passages they follow:
   of every (piece, vertex) slot (Section 3.2, Eq. 4), and the type-I /
   type-II identical-vertex classes of Section 3.3.3 restricted to equal reach
   (the paper leaves reach and ident together unspecified; equal-reach-only
-  merging is the reading taken).
+  merging is the default reading, and ``STEP_U`` gives the classes of the
+  other reading, keyed on the neighbourhood alone).
 """
 from __future__ import annotations
 
@@ -40,6 +41,7 @@ _lock = threading.Lock()
 _lib = None
 
 STEP_D, STEP_A, STEP_I = 1, 2, 4
+STEP_U = 32  # with STEP_I: classes keyed on the neighbourhood alone (any reach)
 
 _i64p = ctypes.POINTER(ctypes.c_int64)
 
@@ -225,7 +227,9 @@ def shatter(g, steps: int = STEP_D | STEP_A | STEP_I) -> list[Piece]:
     * reach of every slot (Section 3.2, Eq. 4), see ``oracle_reach``.
     * I (identical vertices, Section 3.3.3): inside each piece, vertices with
       the same open neighbourhood (type I) or the same closed neighbourhood
-      (type II) within the piece, and the same reach, form a class.
+      (type II) within the piece, and the same reach, form a class; with U
+      as well, the reach is left out of the key (the section does not settle
+      how reach and ident combine; both readings are offered).
     """
     n = g.n
     keep = two_core(g) if steps & STEP_D else np.ones(n, dtype=bool)
@@ -260,7 +264,7 @@ def shatter(g, steps: int = STEP_D | STEP_A | STEP_I) -> list[Piece]:
                 grp = defaultdict(list)
                 for v in p:
                     key = (nb_open[v] | {v}) if closed else nb_open[v]
-                    grp[(key, rmap[v])].append(v)
+                    grp[(key, None if steps & STEP_U else rmap[v])].append(v)
                 classes += [tuple(sorted(c)) for c in grp.values() if len(c) >= 2]
         out.append(Piece(tuple(p), rmap, tuple(sorted(classes)), int(ccsize[cc[p[0]]])))
     return out

@@ -316,7 +316,7 @@ static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t st
   {
     StageTimer tm(ctx.stream);
     tm.start();
-    BCS_TRY(device_merge(ctx, S->pc, I, &S->merged));
+    BCS_TRY(device_merge(ctx, S->pc, I, (steps & BCS_STEP_U) != 0, &S->merged));
     ctx.stats.ms_ident = tm.stop_ms();
   }
   tr.mark("merge");
@@ -361,6 +361,7 @@ static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double 
   bi.col = m.mcol.p;
   bi.reach = (steps & (BCS_STEP_D | BCS_STEP_A)) ? m.mreach.p : nullptr;
   bi.ident = (steps & BCS_STEP_I) ? m.mident.p : nullptr;
+  bi.init = m.minit.p;  // classes of unequal reach only
   bi.bcp = m.mcorr.p;  // starts with the identical-vertex terms
   BcPlanOpts po;
   po.fp32_delta = o && o->delta_fp32;
@@ -379,7 +380,7 @@ static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double 
     StageTimer tm(ctx.stream);
     tm.start();
     BCS_TRY(launch_bc_init(ctx, h->n, S.bcpre.p, d_bc));
-    BCS_TRY(launch_mapback(ctx, m.nslots, m.slot_org.p, m.slot_to_m.p, m.mcorr.p, d_bc));
+    BCS_TRY(launch_mapback(ctx, m.nslots, m.slot_org.p, m.slot_to_m.p, m.mcorr.p, d_bc, m.slot_corr.p));
     ctx.stats.ms_mapback = tm.stop_ms();
   }
   tr.mark("mapback");
@@ -475,14 +476,18 @@ __attribute__((visibility("default"))) int bcs_bc_shattered(const bcs_csr *csr, 
     set_error("bc_out is NULL");
     return BCS_EINVAL;
   }
-  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_O | BCS_STEP_S))) {
+  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_O | BCS_STEP_S | BCS_STEP_U))) {
     set_error("unknown bits in opts->steps");
+    return BCS_EINVAL;
+  }
+  if (opts && (opts->steps & BCS_STEP_S) && (opts->steps & BCS_STEP_U)) {
+    set_error("BCS_STEP_S and BCS_STEP_U cannot be combined");
     return BCS_EINVAL;
   }
   return guarded(opts, [&](Ctx &ctx) {
     if (opts && (opts->steps & BCS_STEP_O)) {
       bcs_opts o2 = *opts;
-      o2.steps &= BCS_STEPS_ALL | BCS_STEP_S;
+      o2.steps &= BCS_STEPS_ALL | BCS_STEP_S | BCS_STEP_U;
       return with_bfs_order(ctx, csr, bc_out, [&](const bcs_csr *h2, double *bc2, const int32_t *) {
         return shattered_impl(ctx, h2, &o2, bc2);
       });
@@ -509,7 +514,8 @@ __attribute__((visibility("default"))) int bcs_bc_shattered_batch(const int64_t 
       set_error("graph_vtx_off must be ascending");
       return BCS_EINVAL;
     }
-  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_S))) {
+  if (opts && ((opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_S | BCS_STEP_U)) ||
+                ((opts->steps & BCS_STEP_S) && (opts->steps & BCS_STEP_U)))) {
     set_error("unknown bits in opts->steps");
     return BCS_EINVAL;
   }

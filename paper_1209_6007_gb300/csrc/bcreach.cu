@@ -122,6 +122,7 @@ struct Weights {  // global-memory path: the int32 arrays; shared path: only the
   const int32_t *ident;   // local, nullable
   const double *init_d;   // reach - 1 as FP64, nullable (converted on the fly)
   const double *ident_d;  // ident as FP64, nullable
+  bool frac;              // init_d may be fractional: never read reach as an integer
 };
 
 struct Debug {
@@ -331,7 +332,8 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
   // the source's weight reach[s] * ident[s] waits in shared memory: read
   // per vertex, it is never recomputed (FP64) inside the divergent loop
   if (g.rank == 0)
-    st.red[RED_WS] = (double)((REACH ? reach_i(s) : 1ll) * (IDENT ? ident_i(s) : 1ll));
+    st.red[RED_WS] = (REACH && wt.frac) ? (wt.init_d[s] + 1.0) * (double)(IDENT ? ident_i(s) : 1ll)
+                                        : (double)((REACH ? reach_i(s) : 1ll) * (IDENT ? ident_i(s) : 1ll));
   g.sync();
   // ---------------------------------------------------------- phase 2
   unsigned long long ndag = 0;
@@ -413,7 +415,8 @@ __device__ void bcreach_source(const Group &g, const int32_t s, const int32_t n,
             }
           }
         }
-        const float df = fmaf(mv, sum, REACH ? (float)(reach_i(v) - 1) : 0.0f);
+        const float df =
+            fmaf(mv, sum, REACH ? (wt.frac ? (float)wt.init_d[v] : (float)(reach_i(v) - 1)) : 0.0f);
         dv = (double)df;
         if (l > 0) {
           const float kv = IDENT ? (float)ident_i(v) : 1.0f;
@@ -471,8 +474,8 @@ template <bool REACH, bool IDENT, bool FP32>
 __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     const SmallItem *__restrict__ items, int nitems, int *item_counter, const CompDesc *__restrict__ comps,
     const int64_t *__restrict__ g_row, const int32_t *__restrict__ g_col, const int32_t *__restrict__ g_reach,
-    const int32_t *__restrict__ g_ident, const int64_t *__restrict__ srcs, double *bcp, int32_t *lvl_scratch,
-    int lvl_stride, int *err, unsigned long long *dag_total) {
+    const int32_t *__restrict__ g_ident, const double *__restrict__ g_init, const int64_t *__restrict__ srcs,
+    double *bcp, int32_t *lvl_scratch, int lvl_stride, int *err, unsigned long long *dag_total) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   __shared__ int s_qtail[SMALL_MAX_GROUPS];
@@ -510,7 +513,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     for (int v = tid; v <= n; v += SMALL_THREADS) row[v] = (int32_t)(g_row[c.row_off + v] - r0);
     for (int e = tid; e < nnz; e += SMALL_THREADS) col[e] = (uint16_t)g_col[r0 + e];
     for (int v = tid; v < n; v += SMALL_THREADS) {
-      if (REACH) init_d[v] = (double)(g_reach[c.vtx_off + v] - 1);
+      if (REACH) init_d[v] = g_init ? g_init[c.vtx_off + v] : (double)(g_reach[c.vtx_off + v] - 1);
       if (IDENT) ident_d[v] = (double)g_ident[c.vtx_off + v];
     }
     // zero every group's accumulator
@@ -543,7 +546,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.lvl_exp = lv + lvl_stride;
     st.qtail = &s_qtail[gid];
     st.red = s_red[gid];
-    Weights wt{nullptr, nullptr, init_d, ident_d};
+    Weights wt{nullptr, nullptr, init_d, ident_d, g_init != nullptr};
     for (int i = item.s_begin + gid; in_group && i < item.s_end; i += ng) {
       const int32_t s = (srcs && c.src_off >= 0) ? (int32_t)srcs[c.src_off + i] : i;
       bcreach_source<REACH, IDENT, FP32, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr, dag);
@@ -584,8 +587,8 @@ template <bool REACH, bool IDENT, bool FP32>
 __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
     const LargeSrc *__restrict__ work, int64_t nwork, unsigned long long *counter, const CompDesc *__restrict__ comps,
     const int64_t *__restrict__ g_row, const int32_t *__restrict__ g_col, const int32_t *__restrict__ g_reach,
-    const int32_t *__restrict__ g_ident, double *bcp, LargeScratch sc, int *err, Debug dbg_in, int use_dbg,
-    unsigned long long *dag_total, int *lmax) {
+    const int32_t *__restrict__ g_ident, const double *__restrict__ g_init, double *bcp, LargeScratch sc, int *err,
+    Debug dbg_in, int use_dbg, unsigned long long *dag_total, int *lmax) {
   __shared__ unsigned long long s_idx;
   __shared__ int s_qtail;
   __shared__ double s_red[16];
@@ -621,7 +624,8 @@ __global__ void __launch_bounds__(LARGE_THREADS) k_bcreach_large(
     cur = next;
     if (next < 0) break;
     const CompDesc c = comps[cur];
-    Weights wt{REACH ? g_reach + c.vtx_off : nullptr, IDENT ? g_ident + c.vtx_off : nullptr, nullptr, nullptr};
+    Weights wt{REACH && !g_init ? g_reach + c.vtx_off : nullptr, IDENT ? g_ident + c.vtx_off : nullptr,
+               REACH && g_init ? g_init + c.vtx_off : nullptr, nullptr, g_init != nullptr};
     bcreach_source<REACH, IDENT, FP32, true>(g, work[idx].s, c.n, g_row + c.row_off, g_col, wt, st, acc, c.fan, err,
                                              use_dbg ? &dbg_in : nullptr, dag, lmax);
   }
@@ -694,7 +698,7 @@ static int launch_small_t(Ctx &ctx, int grid, size_t smem, const SmallItem *item
   BCS_TRY(recip_table_ready(ctx.device));
   auto kern = k_bcreach_small<R, I, F>;
   kern<<<grid, SMALL_THREADS, smem, ctx.stream>>>(items, nitems, counter, comps, in.row, in.col, in.reach, in.ident,
-                                                 srcs, in.bcp, lvl, lvl_stride, err, dag);
+                                                 in.init, srcs, in.bcp, lvl, lvl_stride, err, dag);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;
@@ -705,8 +709,8 @@ static int launch_large_t(Ctx &ctx, int grid, const LargeSrc *work, int64_t nwor
                           const CompDesc *comps, const BcInput &in, const LargeScratch &sc, int *err,
                           const Debug &dbg, int use_dbg, unsigned long long *dag, int *lmax = nullptr) {
   k_bcreach_large<R, I, F><<<grid, LARGE_THREADS, 0, ctx.stream>>>(work, nwork, counter, comps, in.row, in.col,
-                                                                  in.reach, in.ident, in.bcp, sc, err, dbg, use_dbg,
-                                                                  dag, lmax);
+                                                                  in.reach, in.ident, in.init, in.bcp, sc, err, dbg,
+                                                                  use_dbg, dag, lmax);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;
@@ -749,7 +753,7 @@ static void remember_split(long long key, int choice) {
 
 int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &in, const BcPlanOpts &po) {
   Tracer tr("bcreach", ctx.stream);
-  const bool R = in.reach != nullptr, I = in.ident != nullptr, F = po.fp32_delta;
+  const bool R = in.reach != nullptr || in.init != nullptr, I = in.ident != nullptr, F = po.fp32_delta;
   const bool dbg = po.dbg_d || po.dbg_sig || po.dbg_exp || po.dbg_delta;
   const int64_t C = (int64_t)comps_in.size();
   if (po.sources && (C != 1 || po.srcmap)) {

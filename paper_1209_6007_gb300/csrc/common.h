@@ -165,12 +165,18 @@ struct DevMerged {
   DBuf<double> mcorr;        // nmerged
   DBuf<int32_t> slot_org;    // nslots (pre-merge)
   DBuf<int32_t> slot_to_m;   // nslots -> merged vertex
+  // classes of unequal reach only: the merged vertex's dependency start
+  // (sum of its members' reach) / ident - 1, and each copy's own terms
+  DBuf<double> minit;        // nmerged
+  DBuf<double> slot_corr;    // nslots
   std::vector<int64_t> h_piece_off;  // host copies for planning
   std::vector<int64_t> h_piece_ent;  // entries per piece
   std::vector<int32_t> h_piece_maxdeg;  // largest degree per piece before merging
 };
 
-int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out);
+// identical: merge identical vertices; unequal: key classes on the
+// neighbourhood alone (members may differ in reach)
+int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerged *out);
 
 // ------------------------------------------------------- graph kernels
 int launch_validate(Ctx &ctx, const DevGraph &g, int *d_flags);
@@ -179,8 +185,9 @@ int launch_cc(Ctx &ctx, const DevGraph &g, int32_t *d_label, int64_t *d_N);
 int run_peel(Ctx &ctx, const DevGraph &g, const int64_t *d_N, uint8_t *d_alive, int32_t *d_reach,
              int64_t *d_bcpre);
 int launch_bc_init(Ctx &ctx, int64_t n, const int64_t *d_bcpre, double *d_bc);
+// bc[org of slot] += bcp[merged vertex of slot] (+ slot_corr[slot], nullable)
 int launch_mapback(Ctx &ctx, int64_t nslots, const int32_t *slot_org, const int32_t *slot_to_m,
-                   const double *bcp, double *d_bc);
+                   const double *bcp, double *d_bc, const double *slot_corr = nullptr);
 int launch_fill_i32(Ctx &ctx, int32_t *p, int64_t n, int32_t v);
 int launch_fill_i64(Ctx &ctx, int64_t *p, int64_t n, int64_t v);
 int launch_add_f64(Ctx &ctx, double *dst, const double *src, int64_t n);
@@ -217,6 +224,10 @@ struct BcInput {
   const int32_t *col = nullptr;   // local neighbour ids
   const int32_t *reach = nullptr; // nullable (all 1)
   const int32_t *ident = nullptr; // nullable (all 1)
+  // nullable: the dependency start reach - 1 as FP64, possibly fractional
+  // (a class of unequal reaches merged into one vertex); when given it
+  // replaces reach, and the source weight is (init + 1) * ident
+  const double *init = nullptr;
   double *bcp = nullptr;          // accumulation target, indexed by vertex
 };
 

@@ -375,17 +375,19 @@ int launch_bc_init(Ctx &ctx, int64_t n, const int64_t *d_bcpre, double *d_bc) {
 // Eq. 5: bc[v] += bc'[v'] for every copy v' of v (a merged vertex stands for
 // each of its members, so every pre-merge slot reads its merged vertex).
 __global__ void k_mapback(int64_t nslots, const int32_t *__restrict__ slot_org, const int32_t *__restrict__ slot_to_m,
-                          const double *__restrict__ bcp, double *bc) {
+                          const double *__restrict__ bcp, const double *__restrict__ slot_corr, double *bc) {
   for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nslots; p += (int64_t)gridDim.x * blockDim.x) {
     double x = bcp[slot_to_m[p]];
+    if (slot_corr) x += slot_corr[p];
     if (x != 0.0) atomicAdd(bc + slot_org[p], x);
   }
 }
 
 int launch_mapback(Ctx &ctx, int64_t nslots, const int32_t *slot_org, const int32_t *slot_to_m, const double *bcp,
-                   double *d_bc) {
+                   double *d_bc, const double *slot_corr) {
   if (nslots == 0) return BCS_OK;
-  k_mapback<<<grid_for(nslots, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(nslots, slot_org, slot_to_m, bcp, d_bc);
+  k_mapback<<<grid_for(nslots, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(nslots, slot_org, slot_to_m, bcp,
+                                                                             slot_corr, d_bc);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;

@@ -3,10 +3,11 @@
 //
 // Within a piece, vertices u and v are type-I identical when their open
 // neighbourhoods are equal and type-II identical when their closed
-// neighbourhoods are equal.  Only vertices of equal reach are merged (the
-// paper leaves reach and ident together unspecified; with equal reach every
-// member keeps the same dependency initialisation reach - 1 and the same
-// source weight, so one representative stands for all of them).
+// neighbourhoods are equal.  By default only vertices of equal reach are
+// merged (the paper leaves reach and ident together unspecified; with equal
+// reach every member keeps the same dependency initialisation reach - 1 and
+// the same source weight, so one representative stands for all of them);
+// the `unequal` option keys classes on the neighbourhood alone (below).
 //
 // Detection (Section 3.4 uses a neighbourhood hash and explicit comparison
 // on collision): every slot gets an order-free 64-bit hash of its open
@@ -25,6 +26,20 @@
 //                               go through one common neighbour, shared
 //                               equally: "equally distributed among the
 //                               neighbors", Section 3.3.3)
+//
+// With `unequal`, classes are keyed on the neighbourhood alone and members
+// may differ in reach r_i (R = sum r_i, Q = sum r_i^2 over the class).  In
+// Bc-Reach a member i as a target contributes r_i + X (X the part from
+// beyond it, the same for all members), so the merged vertex carries the
+// target weight R + K X: that is Bc-Reach with the fractional dependency
+// start R / K - 1 (and source weight R).  What differs per member becomes a
+// closed form on each copy:
+//   member i:                   (r_i - 1)(R - r_i)  [pairs from the other
+//                               members' sides into i's own side]
+//                               + (r_i - R/K)(N_C - R)  [its own start
+//                               against the sources outside the class]
+//   type I, every neighbour:    (R^2 - Q) / K_N
+// (both reduce to the equal-reach terms when every r_i = r).
 #include "common.h"
 
 namespace bcs {
@@ -55,7 +70,7 @@ __global__ void k_ident_hash(int64_t nslots, const int64_t *__restrict__ srow, c
     for (int64_t k = b; k < e; k++) h += fmix64((uint64_t)org[scol[k]] + 1);
     const uint64_t hc = h + fmix64((uint64_t)org[x] + 1);
     const uint64_t tag = fmix64(((uint64_t)(uint32_t)piece[x] << 32) ^ (uint64_t)(e - b)) ^
-                         fmix64((uint64_t)(uint32_t)reach[x] * 0x9E3779B97F4A7C15ULL + 7);
+                         fmix64((uint64_t)(uint32_t)(reach ? reach[x] : 0) * 0x9E3779B97F4A7C15ULL + 7);
     uint64_t fo = fmix64(h ^ tag), fc = fmix64(hc ^ tag ^ 0xD6E8FEB86659FD93ULL);
     fp_open[x] = fo ? fo : 1;
     fp_closed[x] = fc ? fc : 1;
@@ -128,7 +143,7 @@ __global__ void k_ident_verify(int64_t nslots, const int64_t *__restrict__ srow,
     for (int t = 0; t < 2 && rep == x; t++) {
       const int32_t c = (int32_t)(vals[slot_of[2 * x + t]] & 0xffffffffull);
       if (c == x) continue;
-      if (piece[c] != piece[x] || reach[c] != reach[x]) continue;
+      if (piece[c] != piece[x] || (reach && reach[c] != reach[x])) continue;
       bool ok = t ? rows_equal_closed(srow, scol, x, c) : rows_equal_open(srow, scol, x, c);
       if (ok) {
         rep = c;
@@ -164,6 +179,44 @@ __global__ void k_ident_corr(int64_t nslots, const int64_t *__restrict__ srow, c
   }
 }
 
+// unequal reach: R and Q of every class, on its representative
+__global__ void k_ident_sums(int64_t nslots, const int32_t *__restrict__ cls, const int32_t *__restrict__ reach,
+                             unsigned long long *rsum, unsigned long long *qsum) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nslots; x += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long r = (unsigned long long)reach[x];
+    atomicAdd(rsum + cls[x], r);
+    atomicAdd(qsum + cls[x], r * r);
+  }
+}
+
+// unequal reach: the neighbour terms (on representatives, as corr) and each
+// copy's own terms (slot_corr); N[p] = size of piece p's connected component
+__global__ void k_ident_corr_unequal(int64_t nslots, const int64_t *__restrict__ srow,
+                                     const int32_t *__restrict__ scol, const int32_t *__restrict__ reach,
+                                     const int32_t *__restrict__ piece, const int64_t *__restrict__ N,
+                                     const int32_t *__restrict__ cls, const int32_t *__restrict__ cnt,
+                                     const int8_t *__restrict__ typ, const unsigned long long *__restrict__ rsum,
+                                     const unsigned long long *__restrict__ qsum, double *corr, double *slot_corr) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nslots; x += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t c = cls[x];
+    const int64_t K = cnt[c];
+    if (K < 2) {
+      slot_corr[x] = 0.0;
+      continue;
+    }
+    const int64_t R = (int64_t)rsum[c], r = reach[x], NC = N[piece[x]];
+    slot_corr[x] = (double)((r - 1) * (R - r)) + ((double)r - (double)R / (double)K) * (double)(NC - R);
+    if (c == x && typ[c] == 1) {
+      const int64_t b = srow[c], e = srow[c + 1];
+      const double amt = (double)(R * R - (int64_t)qsum[c]) / (double)(e - b);
+      for (int64_t k = b; k < e; k++) {
+        const int32_t y = scol[k];
+        if (cls[y] == y) atomicAdd(corr + y, amt);
+      }
+    }
+  }
+}
+
 // keep[x] = 1 for class representatives; ndeg[x] = their degree after merging
 __global__ void k_merge_degrees(int64_t nslots, const int64_t *__restrict__ srow, const int32_t *__restrict__ scol,
                                 const int32_t *__restrict__ cls, int64_t *keep, int64_t *ndeg) {
@@ -185,8 +238,9 @@ __global__ void k_merge_emit(int64_t nslots, const int64_t *__restrict__ srow, c
                              const int64_t *__restrict__ piece_off, const int64_t *__restrict__ mslot,
                              const int64_t *__restrict__ mrow_scan, const int32_t *__restrict__ org,
                              const int32_t *__restrict__ reach, const int32_t *__restrict__ cnt,
-                             const double *__restrict__ corr, int64_t *mrow, int32_t *mcol, int32_t *morg,
-                             int32_t *mreach, int32_t *mident, double *mcorr, int32_t *slot_to_m) {
+                             const double *__restrict__ corr, const unsigned long long *__restrict__ rsum,
+                             int64_t *mrow, int32_t *mcol, int32_t *morg, int32_t *mreach, int32_t *mident,
+                             double *mcorr, double *minit, int32_t *slot_to_m) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nslots; x += (int64_t)gridDim.x * blockDim.x) {
     slot_to_m[x] = (int32_t)mslot[cls[x]];
     if (cls[x] != x) continue;
@@ -202,6 +256,7 @@ __global__ void k_merge_emit(int64_t nslots, const int64_t *__restrict__ srow, c
     mreach[m] = reach[x];
     mident[m] = cnt ? cnt[x] : 1;
     mcorr[m] = corr ? corr[x] : 0.0;
+    if (minit) minit[m] = (double)rsum[x] / (double)(cnt ? cnt[x] : 1) - 1.0;
   }
 }
 
@@ -220,7 +275,8 @@ __global__ void k_iota32(int64_t n, int32_t *p) {
     p[i] = (int32_t)i;
 }
 
-int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
+int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerged *out) {
+  unequal = unequal && identical;
   const int64_t P = pc.npieces, S = pc.nslots;
   out->npieces = P;
   out->nslots = S;
@@ -235,6 +291,7 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
   DBuf<int32_t> cls, cnt;
   DBuf<int8_t> typ;
   DBuf<double> corr;
+  DBuf<unsigned long long> rsum, qsum;
   BCS_TRY(cls.alloc(S, ctx.stream));
   if (identical && S > 0) {
     DBuf<uint64_t> fo, fc;
@@ -255,12 +312,26 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
     BCS_CUDA(cudaMemsetAsync(cnt.p, 0, S * sizeof(int32_t), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(typ.p, 0, S * sizeof(int8_t), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(corr.p, 0, S * sizeof(double), ctx.stream));
-    k_ident_hash<<<gs, block, 0, ctx.stream>>>(S, srow, scol, out->slot_org.p, sreach, spiece, fo.p, fc.p);
+    const int32_t *key_reach = unequal ? nullptr : sreach;  // reach is part of the class key unless unequal
+    k_ident_hash<<<gs, block, 0, ctx.stream>>>(S, srow, scol, out->slot_org.p, key_reach, spiece, fo.p, fc.p);
     k_ident_insert<<<gs, block, 0, ctx.stream>>>(S, fo.p, fc.p, out->slot_org.p, keys.p, vals.p, tsize - 1, slot_of.p);
-    k_ident_verify<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, spiece, vals.p, slot_of.p, cls.p, typ.p);
+    k_ident_verify<<<gs, block, 0, ctx.stream>>>(S, srow, scol, key_reach, spiece, vals.p, slot_of.p, cls.p, typ.p);
     k_ident_count<<<gs, block, 0, ctx.stream>>>(S, cls.p, cnt.p);
-    k_ident_corr<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, cls.p, cnt.p, typ.p, corr.p);
-    ctx.launches += 5;
+    ctx.launches += 4;
+    if (unequal) {
+      BCS_TRY(rsum.alloc(S, ctx.stream));
+      BCS_TRY(qsum.alloc(S, ctx.stream));
+      BCS_TRY(out->slot_corr.alloc(S, ctx.stream));
+      BCS_CUDA(cudaMemsetAsync(rsum.p, 0, S * sizeof(unsigned long long), ctx.stream));
+      BCS_CUDA(cudaMemsetAsync(qsum.p, 0, S * sizeof(unsigned long long), ctx.stream));
+      k_ident_sums<<<gs, block, 0, ctx.stream>>>(S, cls.p, sreach, rsum.p, qsum.p);
+      k_ident_corr_unequal<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, spiece, out->piece_N.p, cls.p, cnt.p,
+                                                         typ.p, rsum.p, qsum.p, corr.p, out->slot_corr.p);
+      ctx.launches += 2;
+    } else {
+      k_ident_corr<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, cls.p, cnt.p, typ.p, corr.p);
+      ctx.launches++;
+    }
     BCS_CUDA(cudaGetLastError());
   } else if (S > 0) {
     k_iota32<<<gs, block, 0, ctx.stream>>>(S, cls.p);
@@ -293,14 +364,16 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, DevMerged *out) {
   BCS_TRY(out->mreach.alloc(M, ctx.stream));
   BCS_TRY(out->mident.alloc(M, ctx.stream));
   BCS_TRY(out->mcorr.alloc(M, ctx.stream));
+  if (unequal) BCS_TRY(out->minit.alloc(M, ctx.stream));
   BCS_TRY(out->slot_to_m.alloc(S, ctx.stream));
   BCS_TRY(out->piece_off.alloc(P + 1, ctx.stream));
   BCS_CUDA(cudaMemcpyAsync(out->mrow.p + M, totals.p + 1, sizeof(int64_t), cudaMemcpyDeviceToDevice, ctx.stream));
   if (S > 0) {
     k_merge_emit<<<gs, block, 0, ctx.stream>>>(S, srow, scol, cls.p, spiece, piece_off, mslot.p, mrow_scan.p,
                                                out->slot_org.p, sreach, identical ? cnt.p : nullptr,
-                                               identical ? corr.p : nullptr, out->mrow.p, out->mcol.p, out->morg.p,
-                                               out->mreach.p, out->mident.p, out->mcorr.p, out->slot_to_m.p);
+                                               identical ? corr.p : nullptr, unequal ? rsum.p : nullptr, out->mrow.p,
+                                               out->mcol.p, out->morg.p, out->mreach.p, out->mident.p, out->mcorr.p,
+                                               unequal ? out->minit.p : nullptr, out->slot_to_m.p);
     ctx.launches++;
   }
   tr.mark("emit");

@@ -92,8 +92,8 @@ template <bool REACH, bool IDENT, bool FP32>
 __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
     const MsBatch *__restrict__ batches, int nbatch, int *counter, const CompDesc *__restrict__ comps,
     const int64_t *__restrict__ g_row, const int32_t *__restrict__ g_col, const int32_t *__restrict__ g_reach,
-    const int32_t *__restrict__ g_ident, const int32_t *__restrict__ srcs, double *bcp, MsScratch S, int *err,
-    unsigned long long *dag_total) {
+    const int32_t *__restrict__ g_ident, const double *__restrict__ g_init, const int32_t *__restrict__ srcs,
+    double *bcp, MsScratch S, int *err, unsigned long long *dag_total) {
   __shared__ int s_batch, s_qtail;
   __shared__ int32_t s_src[32];
   __shared__ double s_ws[32];
@@ -132,12 +132,15 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
     const MsBatch bt = batches[bi];
     const CompDesc c = comps[bt.comp];
     const int64_t *row = g_row + c.row_off;
-    const int32_t *reach = REACH ? g_reach + c.vtx_off : nullptr;
+    const int32_t *reach = REACH && !g_init ? g_reach + c.vtx_off : nullptr;
+    const double *init_f = REACH && g_init ? g_init + c.vtx_off : nullptr;  // fractional reach - 1
     const int32_t *ident = IDENT ? g_ident + c.vtx_off : nullptr;
     if (tid < 32) {
       const int32_t s = tid < bt.count ? (srcs ? srcs[bt.first + tid] : bt.first + tid) : -1;
       s_src[tid] = s;
-      s_ws[tid] = s < 0 ? 0.0 : (REACH ? (double)reach[s] : 1.0) * (IDENT ? (double)ident[s] : 1.0);
+      s_ws[tid] = s < 0 ? 0.0
+                        : (REACH ? (init_f ? init_f[s] + 1.0 : (double)reach[s]) : 1.0) *
+                              (IDENT ? (double)ident[s] : 1.0);
       if (s >= 0) atomicOr(nxt + s, 1u << tid);
     }
     if (tid == 0) s_qtail = 0;
@@ -354,7 +357,7 @@ __global__ void __launch_bounds__(MS_THREADS) k_bcreach_ms(
           }
         }
         if (on) {
-          const double init = REACH ? (double)(reach[v] - 1) : 0.0;
+          const double init = REACH ? (init_f ? init_f[v] : (double)(reach[v] - 1)) : 0.0;
           double dv;
           if (!FP32) {
             if (de != 0) sum64 *= scl;
@@ -395,7 +398,7 @@ static int launch_ms_t(Ctx &ctx, int grid, const MsBatch *batches, int nbatch, i
                        const BcInput &in, const int32_t *srcs, const MsScratch &sc, int *err,
                        unsigned long long *dag) {
   k_bcreach_ms<R, I, F><<<grid, MS_THREADS, 0, ctx.stream>>>(batches, nbatch, counter, comps, in.row, in.col, in.reach,
-                                                             in.ident, srcs, in.bcp, sc, err, dag);
+                                                             in.ident, in.init, srcs, in.bcp, sc, err, dag);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   return BCS_OK;
@@ -490,7 +493,7 @@ int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32
     BCS_CUDA(cudaMemsetAsync(tmp.p, 0, ntot * 8, ctx.stream));
     tin.bcp = tmp.p;
   }
-  BCS_TRY(MS_DISPATCH(in.reach != nullptr, in.ident != nullptr, fp32, ctx, (int)grid, d_batches.p,
+  BCS_TRY(MS_DISPATCH(in.reach != nullptr || in.init != nullptr, in.ident != nullptr, fp32, ctx, (int)grid, d_batches.p,
                       (int)batches.size(), counter.p, d_comps, tin, sources ? d_src.p : nullptr, sc, d_err, d_dag));
   if (may_fail) {
     int h_err = 0;

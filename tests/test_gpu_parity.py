@@ -383,6 +383,63 @@ def test_side_vertices_in_a_batch_and_scaled_articulation(gpu):
     assert gpu.last_stats()["n_side"] > 0
 
 
+# ------------------------------------- identical vertices of unequal reach
+def unequal_graphs():
+    out = [gg.from_edges(8, [(0, 2), (0, 3), (0, 4), (1, 2), (1, 3), (1, 4), (2, 5), (3, 6), (3, 7)]),  # K2,3 + pendants
+           gg.with_twins_and_pendants(gg.chung_lu(400, 2.3, 5, 3), 4, 120, 200, 30)]
+    for seed in range(3):
+        out.append(gg.with_twins_and_pendants(gg.gnp(30 + 7 * seed, 0.08 + 0.02 * seed, seed), seed, 8, 25, 3))
+    return out
+
+
+UNEQUAL_GRAPHS = unequal_graphs()
+
+
+def oracle_merged_count(g, steps):
+    return sum(len(p.vertices) - sum(len(c) - 1 for c in p.classes) for p in oracle.shatter(g, steps))
+
+
+@pytest.mark.parametrize("steps", [ALL, oracle.STEP_D | oracle.STEP_I, oracle.STEP_A | oracle.STEP_I, oracle.STEP_I])
+@pytest.mark.parametrize("g", UNEQUAL_GRAPHS + FAMILIES[-8:], ids=lambda g: g.name)
+def test_unequal_reach_merging_gives_the_same_bc(gpu, g, steps):
+    """Classes keyed on the neighbourhood alone (members of any reach):
+    fractional dependency start in Bc-Reach plus per-copy closed forms give
+    bc unchanged; the merged vertex count is the definition's."""
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, steps=steps, unequal=True), ref) <= TOL64
+    assert gpu.last_stats()["n_merged"] == oracle_merged_count(g, steps | oracle.STEP_U)
+
+
+def test_unequal_reach_merging_merges_more_fp32_device_ordered(gpu):
+    g = UNEQUAL_GRAPHS[1]
+    ref = oracle.bc(g)
+    rp, col = on_device(g)
+    assert rel(gpu.bc_shattered(rp, col, unequal=True, delta_fp32=True).cpu().numpy(), ref) <= TOL32
+    assert rel(gpu.bc_shattered(rp, col, unequal=True, order=True).cpu().numpy(), ref) <= TOL64
+    merged_u = gpu.last_stats()["n_merged"]
+    gpu.bc_shattered(rp, col)
+    assert merged_u < gpu.last_stats()["n_merged"]
+
+
+@pytest.mark.parametrize("path", LARGE_PATHS)
+def test_unequal_reach_merging_on_a_large_piece(gpu, path, monkeypatch):
+    """A piece too large for shared memory: both global-memory kernels take
+    the fractional dependency start and source weight."""
+    monkeypatch.setenv("BCS_LARGE_PATH", path)
+    g = gg.with_twins_and_pendants(gg.chung_lu(3000, 2.3, 6, 5), 6, 900, 1500, 100)
+    ref = oracle.bc(g)
+    for fp32, tol in ((False, TOL64), (True, TOL32)):
+        assert rel(gpu.bc_shattered(g.row_ptr, g.col, unequal=True, delta_fp32=fp32), ref) <= tol
+        assert gpu.last_stats()["n_large_sources"] > 0
+
+
+def test_unequal_reach_merging_in_a_batch(gpu):
+    graphs = UNEQUAL_GRAPHS[:4]
+    g = gg.disjoint_union(*graphs)
+    off = np.cumsum([0] + [x.n for x in graphs])
+    assert rel(gpu.bc_shattered_batch(off, g.row_ptr, g.col, unequal=True), oracle.bc(g)) <= TOL64
+
+
 # --------------------------------------------------------------- errors
 def test_malformed_inputs_rejected(gpu):
     bad = {
