@@ -23,9 +23,9 @@
 //   every member:               (K - 1) r (r - 1)
 //   type I, every neighbour:    K (K - 1) r^2 / K_N,  K_N = the degree of a
 //                               member (all ordered pairs of members' sides
-//                               go through one common neighbour, shared
-//                               equally: "equally distributed among the
-//                               neighbors", Section 3.3.3)
+//                               go through one common neighbour, each one
+//                               taking an equal share, as Section 3.3.3
+//                               spreads the r = 1 pairs)
 //
 // With `unequal`, classes are keyed on the neighbourhood alone and members
 // may differ in reach r_i (R = sum r_i, Q = sum r_i^2 over the class).  In

@@ -1,6 +1,5 @@
-// order.cu - BFS ordering of the input graph (Section 4.1, "Ordering sparse
-// networks"): vertices close in the graph get close ids, so a traversal
-// touches nearby memory.
+// order.cu - BFS ordering of the input graph (Section 4.1): vertices close
+// in the graph get close ids, so a traversal touches nearby memory.
 //
 // Every connected component is searched at once, from its smallest vertex
 // (the component labels are the smallest ids), level by level in one
