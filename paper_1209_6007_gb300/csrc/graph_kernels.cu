@@ -120,9 +120,14 @@ __global__ void k_cc_link_first(int64_t n, const int64_t *__restrict__ rp, const
   }
 }
 
-__global__ void k_cc_compress(int64_t n, int32_t *parent) {
-  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
-    parent[v] = uf_find(parent, (int32_t)v);
+// after the first links: every vertex points at its root, and lab keeps a
+// read-only copy (the first-phase component) for the last pass
+__global__ void k_cc_compress(int64_t n, int32_t *parent, int32_t *lab) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t r = uf_find(parent, (int32_t)v);
+    parent[v] = r;
+    lab[v] = r;
+  }
 }
 
 // one CTA of CC_SAMPLE threads: the most frequent root of a fixed sample
@@ -144,33 +149,40 @@ __global__ void k_cc_sample(int64_t n, const int32_t *__restrict__ parent, int32
 }
 
 // One vertex per thread; the remaining edges of a vertex with more than 32
-// of them are walked by its whole warp instead.
+// of them are walked by its whole warp instead.  An edge inside one
+// first-phase component (same lab) changes nothing and is skipped on two
+// independent read-only loads; only edges between components run the
+// union-find.
 __global__ void k_cc_link_rest(int64_t n, const int64_t *__restrict__ rp, const int32_t *__restrict__ col,
-                               int32_t *parent, const int32_t *__restrict__ dominant) {
+                               int32_t *parent, const int32_t *__restrict__ lab, const int32_t *__restrict__ dominant) {
   const int lane = threadIdx.x & 31;
   const int32_t c = *dominant;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < n; base += stride) {
     const int64_t u = base + lane;  // warp-uniform trip count: `base` is the same across the warp
     int64_t b = 0, e = 0;
-    if (u < n && uf_find(parent, (int32_t)u) != c) {
-      b = rp[u] + CC_FIRST;
-      e = rp[u + 1];
+    int32_t lu = c;
+    if (u < n) {
+      lu = lab[u];
+      if (lu != c) {
+        b = rp[u] + CC_FIRST;
+        e = rp[u + 1];
+      }
     }
     const bool wide = e - b > 32;
     if (!wide)
       for (int64_t k = b; k < e; k++) {
         const int32_t v = col[k];
-        // after the compression most linked pairs already share a parent
-        if (uf_vload(parent + u) != uf_vload(parent + v)) uf_unite(parent, (int32_t)u, v);
+        if (lab[v] != lu) uf_unite(parent, (int32_t)u, v);
       }
     for (unsigned m = __ballot_sync(0xffffffffu, wide); m; m &= m - 1) {
       const int src = __ffs(m) - 1;
       const int64_t wu = __shfl_sync(0xffffffffu, u, src);
+      const int32_t wl = __shfl_sync(0xffffffffu, lu, src);
       const int64_t wb = __shfl_sync(0xffffffffu, b, src), we = __shfl_sync(0xffffffffu, e, src);
       for (int64_t k = wb + lane; k < we; k += 32) {
         const int32_t v = col[k];
-        if (uf_vload(parent + wu) != uf_vload(parent + v)) uf_unite(parent, (int32_t)wu, v);
+        if (lab[v] != wl) uf_unite(parent, (int32_t)wu, v);
       }
     }
   }
@@ -199,18 +211,19 @@ __global__ void k_cc_size(int64_t n, const int32_t *__restrict__ label, const in
 int launch_cc(Ctx &ctx, const DevGraph &g, int32_t *d_label, int64_t *d_N) {
   if (g.n == 0) return BCS_OK;
   DBuf<int64_t> cnt;
-  DBuf<int32_t> parent, dom;
+  DBuf<int32_t> parent, lab, dom;
   BCS_TRY(cnt.alloc(g.n, ctx.stream));
   BCS_TRY(parent.alloc(g.n, ctx.stream));
+  BCS_TRY(lab.alloc(g.n, ctx.stream));
   BCS_TRY(dom.alloc(1, ctx.stream));
   BCS_CUDA(cudaMemsetAsync(cnt.p, 0, g.n * sizeof(int64_t), ctx.stream));
   int block = 256;
   int gv = grid_for(g.n, block, ctx.num_sms * 32);
   k_iota<<<gv, block, 0, ctx.stream>>>(g.n, parent.p);
   k_cc_link_first<<<gv, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p);
-  k_cc_compress<<<gv, block, 0, ctx.stream>>>(g.n, parent.p);
-  k_cc_sample<<<1, CC_SAMPLE, 0, ctx.stream>>>(g.n, parent.p, dom.p);
-  k_cc_link_rest<<<gv, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p, dom.p);
+  k_cc_compress<<<gv, block, 0, ctx.stream>>>(g.n, parent.p, lab.p);
+  k_cc_sample<<<1, CC_SAMPLE, 0, ctx.stream>>>(g.n, lab.p, dom.p);
+  k_cc_link_rest<<<gv, block, 0, ctx.stream>>>(g.n, g.rp, g.col, parent.p, lab.p, dom.p);
   k_cc_finish<<<gv, block, 0, ctx.stream>>>(g.n, parent.p, d_label, (unsigned long long *)cnt.p);
   k_cc_size<<<gv, block, 0, ctx.stream>>>(g.n, d_label, cnt.p, d_N);
   ctx.launches += 7;
