@@ -103,14 +103,19 @@ __global__ void k_roots(int64_t n, const int32_t *__restrict__ adeg, const int32
   }
 }
 
-__global__ void k_bfs_init(int64_t n, const int32_t *__restrict__ adeg, const int32_t *__restrict__ label,
-                           const unsigned long long *__restrict__ root_key, int32_t *level, int32_t *parent,
-                           int32_t *order, unsigned long long *tail) {
+// level: 0 for the roots, LEVEL_NONE for the other live vertices,
+// LEVEL_DEAD for removed ones (so the BFS tests liveness and visits with
+// one load)
+constexpr int32_t LEVEL_NONE = -1, LEVEL_DEAD = -2;
+
+__global__ void k_bfs_init(int64_t n, const uint8_t *__restrict__ alive, const int32_t *__restrict__ adeg,
+                           const int32_t *__restrict__ label, const unsigned long long *__restrict__ root_key,
+                           int32_t *level, int32_t *parent, int32_t *order, unsigned long long *tail) {
   GRID_STRIDE(v, n) {
     const bool root =
         adeg[v] > 0 && (int64_t)(0x7fffffffu - (unsigned)(root_key[label[v]] & 0xffffffffull)) == v;
     parent[v] = root ? -1 : INT32_MAX;  // the BFS takes the minimum over the level above
-    level[v] = root ? 0 : -1;
+    level[v] = root ? 0 : (alive[v] ? LEVEL_NONE : LEVEL_DEAD);
     if (root) push_aggr(order, tail, (int32_t)v);
   }
 }
@@ -174,10 +179,10 @@ __global__ void k_forest_coop(const int64_t *__restrict__ rp, const int32_t *__r
       if (sl == 0 && L > 0) atomicAdd(nchild + uf_vload(parent + v), 1);  // final since the last wait
       for (int64_t k = rp[v] + sl; k < rp[v + 1]; k += FOREST_SUB) {
         const int32_t w = col[k];
-        if (!alive[w]) continue;
         int32_t lw = uf_vload(level + w);
+        if (lw == LEVEL_DEAD) continue;
         if (lw < 0) {
-          lw = atomicCAS(level + w, -1, L + 1);
+          lw = atomicCAS(level + w, LEVEL_NONE, L + 1);
           if (lw < 0) {
             const unsigned mask = __activemask();
             const int leader = __ffs(mask) - 1;
@@ -498,7 +503,7 @@ int device_pieces(Ctx &ctx, const DevGraph &g, const uint8_t *alive, const int32
     BCS_CUDA(cudaMemsetAsync(root_key.p, 0, n * sizeof(unsigned long long), ctx.stream));
     BCS_CUDA(cudaMemsetAsync(tot.p, 0, 2 * sizeof(int64_t), ctx.stream));
     k_roots<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, root_key.p);
-    k_bfs_init<<<gv, B, 0, ctx.stream>>>(n, adeg.p, label, root_key.p, level.p, parent.p, order.p,
+    k_bfs_init<<<gv, B, 0, ctx.stream>>>(n, alive, adeg.p, label, root_key.p, level.p, parent.p, order.p,
                                          (unsigned long long *)tot.p);
     ctx.launches += 2;
     BCS_CUDA(cudaGetLastError());
