@@ -478,6 +478,8 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     double *bcp, int32_t *lvl_scratch, int lvl_stride, int *err, unsigned long long *dag_total) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
+  __shared__ int s_next;                     // the item's next unclaimed source
+  __shared__ int s_claim[SMALL_MAX_GROUPS];  // the source each group claimed last
   __shared__ int s_qtail[SMALL_MAX_GROUPS];
   __shared__ double s_red[SMALL_MAX_GROUPS][16];
   const int tid = threadIdx.x;
@@ -516,6 +518,7 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
       if (REACH) init_d[v] = g_init ? g_init[c.vtx_off + v] : (double)(g_reach[c.vtx_off + v] - 1);
       if (IDENT) ident_d[v] = (double)g_ident[c.vtx_off + v];
     }
+    if (tid == 0) s_next = item.s_begin;
     // zero every group's accumulator
     for (int x = tid; x < ng * n; x += SMALL_THREADS) {
       const int gi = x / n, v = x - gi * n;
@@ -523,12 +526,15 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
       a[v] = 0.0;
     }
     __syncthreads();
-    // whole warps per group; with ng not dividing the CTA's warps the
-    // remaining warps sit out this item
-    const int gsize = 32 * ((SMALL_THREADS / 32) / ng);
-    const int gid = tid / gsize;
-    const bool in_group = gid < ng;
-    Group g{tid % gsize, gsize, 1 + gid};
+    // whole warps per group, every warp in one: group k takes warps
+    // [k W / ng, (k + 1) W / ng), so sizes differ by at most one warp, and
+    // each group claims its next source from the item (a larger group
+    // finishes its sources sooner and takes more of them)
+    constexpr int W = SMALL_THREADS / 32;
+    const int warp = tid >> 5;
+    const int gid = ((warp + 1) * ng - 1) / W;
+    const int w0 = (gid * W) / ng, w1 = ((gid + 1) * W) / ng;
+    Group g{tid - w0 * 32, (w1 - w0) * 32, 1 + gid};
     unsigned char *q = p + per * gid;
     SrcState<FP32, uint16_t> st;
     st.d = (int32_t *)q;
@@ -547,7 +553,13 @@ __global__ void __launch_bounds__(SMALL_THREADS) k_bcreach_small(
     st.qtail = &s_qtail[gid];
     st.red = s_red[gid];
     Weights wt{nullptr, nullptr, init_d, ident_d, g_init != nullptr};
-    for (int i = item.s_begin + gid; in_group && i < item.s_end; i += ng) {
+    for (;;) {
+      // every member reads the claim before the source's first group wait,
+      // so the next claim cannot overwrite it early
+      if (g.rank == 0) s_claim[gid] = atomicAdd(&s_next, 1);
+      g.sync();
+      const int i = s_claim[gid];
+      if (i >= item.s_end) break;
       const int32_t s = (srcs && c.src_off >= 0) ? (int32_t)srcs[c.src_off + i] : i;
       bcreach_source<REACH, IDENT, FP32, false>(g, s, n, row, col, wt, st, acc, c.fan, err, nullptr, dag);
     }
