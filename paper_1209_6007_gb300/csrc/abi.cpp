@@ -27,13 +27,34 @@ StageTimer::~StageTimer() {
   if (a) cudaEventDestroy(a);
   if (b) cudaEventDestroy(b);
 }
-void StageTimer::start() { cudaEventRecord(a, s); }
+void StageTimer::start() {
+  if (!a) {  // handed to the call by stop_into
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+  }
+  cudaEventRecord(a, s);
+}
 double StageTimer::stop_ms() {
   float ms = 0.f;
   cudaEventRecord(b, s);
   cudaEventSynchronize(b);
   cudaEventElapsedTime(&ms, a, b);
   return (double)ms;
+}
+void StageTimer::stop_into(Ctx &ctx, double *dst) {
+  cudaEventRecord(b, s);
+  ctx.pending.push_back(Ctx::Pending{a, b, dst});
+  a = b = nullptr;  // the call owns the events now; a later start() makes new ones
+}
+void resolve_stage_times(Ctx &ctx) {
+  for (const Ctx::Pending &p : ctx.pending) {
+    float ms = 0.f;
+    if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+      *p.dst += (double)ms;
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  ctx.pending.clear();
 }
 
 static double now_ms() {
@@ -178,7 +199,7 @@ static int upload_and_validate(Ctx &ctx, const bcs_csr *h, Input *in, const int6
       BCS_CUDA(cudaMemcpyAsync(in->col.p, h->col, h->nnz * sizeof(int32_t), cudaMemcpyHostToDevice, ctx.stream));
     in->g.rp = in->rp.p;
     in->g.col = in->col.p;
-    ctx.stats.ms_upload = tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_upload);
   }
   StageTimer tm(ctx.stream);
   tm.start();
@@ -195,7 +216,7 @@ static int upload_and_validate(Ctx &ctx, const bcs_csr *h, Input *in, const int6
   int f = 0;
   BCS_CUDA(cudaMemcpyAsync(&f, flags.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
   BCS_CUDA(cudaStreamSynchronize(ctx.stream));
-  ctx.stats.ms_validate = tm.stop_ms();
+  tm.stop_into(ctx, &ctx.stats.ms_validate);
   if (f) {
     std::string m = "malformed CSR:";
     if (f & 1) m += " offsets or ids out of range;";
@@ -218,7 +239,7 @@ static int output_bc(Ctx &ctx, const bcs_csr *h, const double *d_bc, double *bc_
     StageTimer tm(ctx.stream);
     tm.start();
     BCS_CUDA(cudaMemcpyAsync(bc_out, d_bc, h->n * sizeof(double), cudaMemcpyDeviceToHost, ctx.stream));
-    ctx.stats.ms_download = tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_download);
   }
   return BCS_OK;
 }
@@ -291,7 +312,7 @@ static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t st
     StageTimer tm(ctx.stream);
     tm.start();
     BCS_TRY(launch_cc(ctx, in.g, label.p, N.p));
-    ctx.stats.ms_cc = tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_cc);
   }
   {
     StageTimer tm(ctx.stream);
@@ -303,21 +324,21 @@ static int shatter_impl(Ctx &ctx, const bcs_csr *h, const Input &in, uint32_t st
       BCS_TRY(launch_fill_i32(ctx, reach.p, n, 1));
       BCS_CUDA(cudaMemsetAsync(S->bcpre.p, 0, n * sizeof(int64_t), ctx.stream));
     }
-    ctx.stats.ms_peel = tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_peel);
   }
   tr.mark("cc+peel");
   {
     StageTimer tm(ctx.stream);
     tm.start();
     BCS_TRY(device_pieces(ctx, in.g, alive.p, reach.p, N.p, label.p, A, &S->pc));
-    ctx.stats.ms_blocks = tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_blocks);
   }
   tr.mark("pieces");
   {
     StageTimer tm(ctx.stream);
     tm.start();
     BCS_TRY(device_merge(ctx, S->pc, I, (steps & BCS_STEP_U) != 0, &S->merged));
-    ctx.stats.ms_ident = tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_ident);
   }
   tr.mark("merge");
   // component descriptors
@@ -381,7 +402,7 @@ static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double 
     tm.start();
     BCS_TRY(launch_bc_init(ctx, h->n, S.bcpre.p, d_bc));
     BCS_TRY(launch_mapback(ctx, m.nslots, m.slot_org.p, m.slot_to_m.p, m.mcorr.p, d_bc, m.slot_corr.p));
-    ctx.stats.ms_mapback = tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_mapback);
   }
   tr.mark("mapback");
   return output_bc(ctx, h, d_bc, bc_out);
@@ -430,6 +451,7 @@ static int guarded(const bcs_opts *opts, F &&body) {
     int rc = make_ctx(opts, &ctx);
     if (rc != BCS_OK) return rc;
     rc = body(ctx);
+    resolve_stage_times(ctx);
     if (rc == BCS_OK) {
       ctx.stats.ms_total = now_ms() - t0;
       ctx.stats.kernel_launches = ctx.launches;

@@ -1013,7 +1013,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     ctx.stats.small_ng_cap = ng_cap;
     ctx.stats.small_smem_budget = (int64_t)budget;
     BCS_TRY(run_small(items, smem_small, grid_small, in.bcp));
-    ctx.stats.ms_bcreach_small += tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_bcreach_small);
     tr.mark("small");
   }
   // one source per CTA over the given list; *d_lmax (optional) receives the
@@ -1052,7 +1052,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     Debug dbgs{po.dbg_d, po.dbg_sig, po.dbg_exp, po.dbg_delta};
     BCS_TRY(BCS_DISPATCH3(launch_large_t, R, I, F, ctx, (int)grid, d_work.p, (int64_t)w.size(), counter.p, d_comps.p,
                           in, sc, d_err.p, dbgs, dbg ? 1 : 0, d_dag.p, d_lmax));
-    ctx.stats.ms_bcreach_large += tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_bcreach_large);
     return BCS_OK;
   };
   int64_t skip = 0;  // leading sources of each large piece already done
@@ -1088,7 +1088,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     BCS_TRY(run_ms(ctx, comps, large, in, F, po.sources, po.nsources, skip, d_comps.p, d_err.p, d_dag.p,
                    &depth_failed));
     if (depth_failed) build_work(skip);
-    ctx.stats.ms_bcreach_large += tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_bcreach_large);
   }
   if (!work.empty()) BCS_TRY(run_per_source(work, nullptr));
   int h_err = 0;

@@ -76,6 +76,12 @@ struct DBuf {
 
 // ------------------------------------------------------- call context
 struct Ctx {
+  // stage times resolved when the call ends: (start, stop, stat to add to)
+  struct Pending {
+    cudaEvent_t a, b;
+    double *dst;
+  };
+  std::vector<Pending> pending;
   int device = 0;
   int num_sms = 0;
   size_t smem_optin = 0;
@@ -101,8 +107,13 @@ struct StageTimer {
   StageTimer(cudaStream_t stream);
   ~StageTimer();
   void start();
-  double stop_ms();  // synchronises on the stop event
+  double stop_ms();  // synchronises on the stop event (for a choice taken now)
+  // records the stop without waiting; *dst gains the time when the call
+  // ends (resolve_stage_times), so the host runs ahead of the device
+  void stop_into(Ctx &ctx, double *dst);
 };
+// add every pending stage time to its stat and release the events
+void resolve_stage_times(Ctx &ctx);
 
 // Optional per-stage trace: with the environment variable BCS_TRACE set,
 // marks are CUDA events on the call's stream and the gaps between them are

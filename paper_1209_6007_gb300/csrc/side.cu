@@ -247,7 +247,7 @@ int run_bcreach_side(Ctx &ctx, const DevMerged &m, const std::vector<CompDesc> &
   ctx.stats.n_side = nside_total;
   tr.mark("mark+reduce");
   if (nside_total == 0) {
-    ctx.stats.ms_side = tm.stop_ms();
+    tm.stop_into(ctx, &ctx.stats.ms_side);
     return run_bcreach(ctx, comps, in, po);
   }
   DBuf<double> bred;
@@ -276,7 +276,7 @@ int run_bcreach_side(Ctx &ctx, const DevMerged &m, const std::vector<CompDesc> &
     }
     roff += nr;
   }
-  ctx.stats.ms_side = tm.stop_ms();
+  tm.stop_into(ctx, &ctx.stats.ms_side);
   BcInput a = in;
   a.reach = reach2.p;
   BcPlanOpts pa = po;
