@@ -163,6 +163,38 @@ def test_classes_need_equal_reach():
     assert classes_of(pieces) == [(1, 3)]
 
 
+def test_classes_of_any_reach():
+    """With STEP_U the reach leaves the key: in the C4 with a pendant on 0,
+    0 and 2 (same neighbours {1, 3}, reaches 2 and 1) form a class too; on
+    graphs where every reach is equal, or with no removal at all, the
+    classes are exactly the equal-reach ones; and an equal-reach class is
+    always inside a class of any reach."""
+    g = gg.from_edges(5, [(0, 1), (1, 2), (2, 3), (3, 0), (0, 4)])
+    assert classes_of(oracle.shatter(g, DAI | oracle.STEP_U)) == [(0, 2), (1, 3)]
+    for g in (gg.complete_bipartite(2, 3), gg.complete(5), gg.cycle(4)):
+        assert classes_of(oracle.shatter(g, DAI | oracle.STEP_U)) == classes_of(oracle.shatter(g, DAI))
+    for seed in range(4):
+        g = gg.with_twins_and_pendants(gg.gnp(40, 0.1, seed), seed, 8, 25, 3)
+        assert classes_of(oracle.shatter(g, oracle.STEP_I | oracle.STEP_U)) == \
+            classes_of(oracle.shatter(g, oracle.STEP_I))
+        wide = [set(c) for c in classes_of(oracle.shatter(g, DAI | oracle.STEP_U))]
+        for c in classes_of(oracle.shatter(g, DAI)):
+            assert any(set(c) <= w for w in wide)
+
+
+def test_added_side_vertices_have_clique_neighbourhoods():
+    """The side-vertex generator's claim: every added vertex's neighbours
+    are pairwise adjacent in the final graph."""
+    base = gg.gnp(30, 0.15, 4)
+    g = gg.with_side_vertices(base, 5, 25, 20)
+    assert g.n == base.n + 45
+    adj = [set(map(int, g.neighbors(v))) for v in range(g.n)]
+    for v in range(base.n, g.n):
+        nb = sorted(adj[v])
+        assert len(nb) >= 2
+        assert all(b in adj[a] for i, a in enumerate(nb) for b in nb[i + 1:])
+
+
 def test_figure3_identical_vertices_golden():
     """Fig. 3 (Section 3.4): vertices 1 and 8 are identical with neighbours
     {2,4,6,7}; with one of them removed the other is an articulation vertex.
