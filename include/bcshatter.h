@@ -89,6 +89,15 @@ extern "C" {
  * Taken by bcs_bc_shattered and bcs_bc_shattered_batch; not combinable with
  * BCS_STEP_S (BCS_EINVAL). */
 #define BCS_STEP_U 32u
+/* One more articulation split after identical merging (the preprocessing of
+ * Section 3.4 repeated once; merging can leave a merged vertex as a cut
+ * vertex, Fig. 3), opt-in and not part of BCS_STEPS_ALL: the merged pieces
+ * are split into biconnected blocks again, with each merged vertex weighing
+ * reach * ident and a cut copy of a vertex standing for k members carrying
+ * 1/k of the weight beyond it per member.  The result is the same bc.  Taken
+ * by bcs_bc_shattered and bcs_bc_shattered_batch; not combinable with
+ * BCS_STEP_S or BCS_STEP_U (BCS_EINVAL). */
+#define BCS_STEP_L 64u
 
 typedef struct bcs_csr {
   int64_t n;              /* number of vertices */
@@ -156,7 +165,7 @@ int bcs_bc_plain(const bcs_csr *csr, const bcs_opts *opts, double *bc_out);
 
 /*
  * Shattered and compressed BC (Section 3): the steps in opts->steps are
- * applied once in the order D, A, I (then S, if set, on the merged pieces);
+ * applied once in the order D, A, I (then S or L, if set, on the merged pieces);
  * Bc-Reach (Algorithm 2, with the identical-vertex terms of Section 3.3.3,
  * and Algorithm 3's searches for side vertices) runs on every piece; the piece
  * scores are mapped back with Eq. 5 (bc[v] = sum over copies v' of v of

@@ -21,10 +21,10 @@ from dataclasses import dataclass
 import numpy as np
 
 from ._lib import (NOALLOC_MAX_N, BCS_EINVAL, BCS_ENODEV, BCS_ENOMEM, BCS_EOVERFLOW, BCS_ECUDA, BCS_ETIMEOUT, STEP_A, STEP_D,
-                   STEP_I, STEP_O, STEP_S, STEP_U, STEPS_ALL, ComponentsView, Csr, Opts, Stats, load)
+                   STEP_I, STEP_L, STEP_O, STEP_S, STEP_U, STEPS_ALL, ComponentsView, Csr, Opts, Stats, load)
 
 __all__ = ["bc_plain", "bc_plain_noalloc", "bc_shattered_batch", "NOALLOC_MAX_N", "bc_shattered", "bc_sources", "debug_sssp", "shatter", "last_stats", "BcsError", "load",
-           "STEP_D", "STEP_A", "STEP_I", "STEP_O", "STEP_S", "STEP_U", "STEPS_ALL", "version"]
+           "STEP_D", "STEP_A", "STEP_I", "STEP_O", "STEP_S", "STEP_U", "STEP_L", "STEPS_ALL", "version"]
 
 _NAMES = {BCS_EINVAL: "EINVAL", BCS_ENOMEM: "ENOMEM", BCS_ECUDA: "ECUDA", BCS_ETIMEOUT: "ETIMEOUT",
           BCS_EOVERFLOW: "EOVERFLOW", BCS_ENODEV: "ENODEV"}
@@ -110,7 +110,7 @@ def bc_plain(row_ptr, col=None, *, delta_fp32: bool = False, stream=None, order:
 
 def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool = False, stream=None,
                  max_wait: int = 0, autotune: bool = False, order: bool = False, side: bool = False,
-                 unequal: bool = False):
+                 unequal: bool = False, resplit: bool = False):
     """Shattered + compressed BC (Section 3), equal to Eq. 1 on the input.
 
     max_wait bounds the polls of device-side waits (0: default, < 0: give up
@@ -118,9 +118,11 @@ def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool 
     times the small-piece work splits once per shape bucket and reuses the
     fastest.  order=True renumbers the graph in BFS order first (Section 4.1).
     side=True also takes side vertices out of the pieces (Section 3.3.2).
-    unequal=True merges identical vertices whatever their reach."""
+    unequal=True merges identical vertices whatever their reach.
+    resplit=True splits the merged pieces at their cut vertices once more."""
     rp, cl = _csr_of(row_ptr, col)
-    extra = (STEP_O if order else 0) | (STEP_S if side else 0) | (STEP_U if unequal else 0)
+    extra = (STEP_O if order else 0) | (STEP_S if side else 0) | (STEP_U if unequal else 0) | \
+        (STEP_L if resplit else 0)
     a = _Args(rp, cl, steps=steps | extra, delta_fp32=delta_fp32, stream=stream, max_wait=max_wait,
               autotune=autotune)
     out, ptr = a.out(a.n)
@@ -129,14 +131,15 @@ def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool 
 
 
 def bc_shattered_batch(vtx_off, row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool = False,
-                       stream=None, side: bool = False, unequal: bool = False):
+                       stream=None, side: bool = False, unequal: bool = False, resplit: bool = False):
     """BC of many independent graphs packed in one CSR (graph g owns the
     vertices [vtx_off[g], vtx_off[g+1]); no edge may join two graphs).
     side=True also takes side vertices out of the pieces (Section 3.3.2);
-    unequal=True merges identical vertices whatever their reach."""
+    unequal=True merges identical vertices whatever their reach; resplit=True
+    splits the merged pieces at their cut vertices once more."""
     rp, cl = _csr_of(row_ptr, col)
-    a = _Args(rp, cl, steps=steps | (STEP_S if side else 0) | (STEP_U if unequal else 0), delta_fp32=delta_fp32,
-              stream=stream)
+    extra = (STEP_S if side else 0) | (STEP_U if unequal else 0) | (STEP_L if resplit else 0)
+    a = _Args(rp, cl, steps=steps | extra, delta_fp32=delta_fp32, stream=stream)
     off = np.ascontiguousarray(np.asarray(vtx_off, dtype=np.int64).reshape(-1))
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_shattered_batch(off.ctypes.data, off.size - 1, ctypes.byref(a.csr), ctypes.byref(a.opts),

@@ -19,6 +19,7 @@ STEPS_ALL = 7
 STEP_O = 8  # BFS ordering, opt-in
 STEP_S = 16  # side vertices, opt-in
 STEP_U = 32  # identical vertices of unequal reach, opt-in
+STEP_L = 64  # one more articulation split after merging, opt-in
 NOALLOC_MAX_N = 16384
 
 c_i64, c_i32, c_u32, c_dbl, c_vp = ctypes.c_int64, ctypes.c_int32, ctypes.c_uint32, ctypes.c_double, ctypes.c_void_p

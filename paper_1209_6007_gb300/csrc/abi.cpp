@@ -386,7 +386,9 @@ static int shattered_impl(Ctx &ctx, const bcs_csr *h, const bcs_opts *o, double 
   bi.bcp = m.mcorr.p;  // starts with the identical-vertex terms
   BcPlanOpts po;
   po.fp32_delta = o && o->delta_fp32;
-  if (steps & BCS_STEP_S)
+  if (steps & BCS_STEP_L)
+    BCS_TRY(run_bcreach_resplit(ctx, m, bi, po));
+  else if (steps & BCS_STEP_S)
     BCS_TRY(run_bcreach_side(ctx, m, S.comps, bi, po, h->n));
   else
     BCS_TRY(run_bcreach(ctx, S.comps, bi, po));
@@ -431,6 +433,12 @@ static int with_bfs_order(Ctx &ctx, const bcs_csr *h, double *bc_out, F &&run) {
 }
 
 }  // namespace bcs
+
+// steps S, U and L each change the pieces Bc-Reach runs on; at most one
+static bool optional_steps_compatible(uint32_t steps) {
+  const int k = ((steps & BCS_STEP_S) != 0) + ((steps & BCS_STEP_U) != 0) + ((steps & BCS_STEP_L) != 0);
+  return k <= 1;
+}
 
 // ================================================================ C ABI
 using namespace bcs;
@@ -498,18 +506,18 @@ __attribute__((visibility("default"))) int bcs_bc_shattered(const bcs_csr *csr, 
     set_error("bc_out is NULL");
     return BCS_EINVAL;
   }
-  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_O | BCS_STEP_S | BCS_STEP_U))) {
+  if (opts && (opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_O | BCS_STEP_S | BCS_STEP_U | BCS_STEP_L))) {
     set_error("unknown bits in opts->steps");
     return BCS_EINVAL;
   }
-  if (opts && (opts->steps & BCS_STEP_S) && (opts->steps & BCS_STEP_U)) {
-    set_error("BCS_STEP_S and BCS_STEP_U cannot be combined");
+  if (opts && !optional_steps_compatible(opts->steps)) {
+    set_error("at most one of BCS_STEP_S, BCS_STEP_U and BCS_STEP_L");
     return BCS_EINVAL;
   }
   return guarded(opts, [&](Ctx &ctx) {
     if (opts && (opts->steps & BCS_STEP_O)) {
       bcs_opts o2 = *opts;
-      o2.steps &= BCS_STEPS_ALL | BCS_STEP_S | BCS_STEP_U;
+      o2.steps &= BCS_STEPS_ALL | BCS_STEP_S | BCS_STEP_U | BCS_STEP_L;
       return with_bfs_order(ctx, csr, bc_out, [&](const bcs_csr *h2, double *bc2, const int32_t *) {
         return shattered_impl(ctx, h2, &o2, bc2);
       });
@@ -536,8 +544,8 @@ __attribute__((visibility("default"))) int bcs_bc_shattered_batch(const int64_t 
       set_error("graph_vtx_off must be ascending");
       return BCS_EINVAL;
     }
-  if (opts && ((opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_S | BCS_STEP_U)) ||
-                ((opts->steps & BCS_STEP_S) && (opts->steps & BCS_STEP_U)))) {
+  if (opts && ((opts->steps & ~(BCS_STEPS_ALL | BCS_STEP_S | BCS_STEP_U | BCS_STEP_L)) ||
+                !optional_steps_compatible(opts->steps))) {
     set_error("unknown bits in opts->steps");
     return BCS_EINVAL;
   }

@@ -273,6 +273,10 @@ int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32
 // descriptors; their vertex ranges index BcInput's arrays.
 int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po);
 
+// Bc-Reach after one more articulation split of the merged pieces
+// (resplit.cu): in.bcp (the merged vertices' bc') gains the new pieces' bc'.
+int run_bcreach_resplit(Ctx &ctx, DevMerged &m, const BcInput &in, const BcPlanOpts &po);
+
 // Bc-Reach over the merged pieces with side vertices taken out (side.cu):
 // the same bc' as run_bcreach(comps, in, po), with in.bcp accumulated.
 // n_graph: vertices of the input graph (a bound on reach).

@@ -84,25 +84,29 @@ def test_host_side_argument_checks():
 
 
 def test_step_bits_checked_on_the_host():
-    """BCS_STEP_S and BCS_STEP_U are taken by the shattered calls (not
-    together), BCS_STEP_O by all but the batch call, and unknown bits are
-    rejected before any device work."""
+    """BCS_STEP_S, BCS_STEP_U and BCS_STEP_L are taken by the shattered calls
+    (at most one of them), BCS_STEP_O by all but the batch call, and unknown
+    bits are rejected before any device work."""
     import paper_1209_6007_gb300 as bcs
     rp, col = np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32)
-    for steps in (64, 128 | bcs.STEP_S, bcs.STEPS_ALL | bcs.STEP_S | bcs.STEP_U):
+    pairs = (bcs.STEP_S | bcs.STEP_U, bcs.STEP_S | bcs.STEP_L, bcs.STEP_U | bcs.STEP_L)
+    for steps in (128, 256 | bcs.STEP_S) + tuple(bcs.STEPS_ALL | p for p in pairs):
         with pytest.raises(bcs.BcsError) as e:
             bcs.bc_shattered(rp, col, steps=steps)
         assert e.value.code == bcs.BCS_EINVAL
-    for steps in (bcs.STEPS_ALL | bcs.STEP_O, bcs.STEPS_ALL | bcs.STEP_S | bcs.STEP_U):
+    for steps in (bcs.STEPS_ALL | bcs.STEP_O,) + tuple(bcs.STEPS_ALL | p for p in pairs):
         with pytest.raises(bcs.BcsError) as e:
             bcs.bc_shattered_batch([0, 2], rp, col, steps=steps)
         assert e.value.code == bcs.BCS_EINVAL
-    with pytest.raises(bcs.BcsError) as e:  # the pieces API has no unequal-reach classes
-        bcs.shatter(rp, col, steps=bcs.STEPS_ALL | bcs.STEP_U)
-    assert e.value.code == bcs.BCS_EINVAL
+    for steps in (bcs.STEP_U, bcs.STEP_L):  # the pieces API has neither
+        with pytest.raises(bcs.BcsError) as e:
+            bcs.shatter(rp, col, steps=bcs.STEPS_ALL | steps)
+        assert e.value.code == bcs.BCS_EINVAL
     for call in (lambda: bcs.bc_shattered(rp, col, side=True),
                  lambda: bcs.bc_shattered(rp, col, side=True, order=True),
                  lambda: bcs.bc_shattered(rp, col, unequal=True, order=True),
+                 lambda: bcs.bc_shattered(rp, col, resplit=True, order=True),
+                 lambda: bcs.bc_shattered_batch([0, 2], rp, col, resplit=True),
                  lambda: bcs.bc_shattered_batch([0, 2], rp, col, side=True),
                  lambda: bcs.bc_shattered_batch([0, 2], rp, col, unequal=True)):
         try:

@@ -440,6 +440,72 @@ def test_unequal_reach_merging_in_a_batch(gpu):
     assert rel(gpu.bc_shattered_batch(off, g.row_ptr, g.col, unequal=True), oracle.bc(g)) <= TOL64
 
 
+# --------------------------- one more articulation split after merging
+def twins_joining(seed, k, pend=0):
+    """Two random 2-connected parts joined only through k open twins (each
+    adjacent to the same vertices of both parts): biconnected as given, and
+    the twins' merged vertex is a cut vertex (the situation of Fig. 3)."""
+    rng = np.random.default_rng(seed)
+    na, nb = int(rng.integers(4, 12)), int(rng.integers(4, 12))
+    e = []
+    for off, m in ((0, na), (na, nb)):
+        e += [(off + i, off + (i + 1) % m) for i in range(m)]
+        e += [(off + int(a), off + int(b)) for a, b in rng.integers(0, m, (int(rng.integers(0, 4)), 2)) if a != b]
+    S = list(rng.choice(na, 2, replace=False)) + list(na + rng.choice(nb, 2, replace=False))
+    n = na + nb
+    e += [(n + t, int(x)) for t in range(k) for x in S]
+    n += k
+    for _ in range(pend):
+        e.append((int(rng.integers(0, n)), n))
+        n += 1
+    e = {(min(a, b), max(a, b)) for a, b in e}
+    return gg.from_edges(n, sorted(e), f"twins_joining({seed},{k},{pend})")
+
+
+RESPLIT_GRAPHS = [twins_joining(s, k, p) for s, k, p in ((1, 2, 0), (2, 3, 0), (3, 4, 6), (4, 2, 10), (5, 3, 4))]
+
+
+@pytest.mark.parametrize("steps", [ALL, oracle.STEP_A | oracle.STEP_I, oracle.STEP_I, oracle.STEP_D | oracle.STEP_A])
+@pytest.mark.parametrize("g", RESPLIT_GRAPHS + FAMILIES[-8:], ids=lambda g: g.name)
+def test_resplit_gives_the_same_bc(gpu, g, steps):
+    """The merged pieces split again at their cut vertices (a merged cut
+    vertex's copies carry 1/k of the weight beyond it per member): bc
+    unchanged."""
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, steps=steps, resplit=True), ref) <= TOL64
+
+
+def test_resplit_splits_at_merged_twins(gpu):
+    g = RESPLIT_GRAPHS[1]
+    gpu.bc_shattered(g.row_ptr, g.col)
+    before = gpu.last_stats()["n_pieces"]
+    gpu.bc_shattered(g.row_ptr, g.col, resplit=True)
+    assert gpu.last_stats()["n_pieces"] > before
+
+
+def test_resplit_larger_graphs_fp32_device_ordered_and_batch(gpu):
+    for g in (gg.config(1), gg.config(2, scale_pct=3),
+              gg.with_twins_and_pendants(gg.chung_lu(400, 2.3, 5, 3), 4, 120, 200, 30)):
+        ref = oracle.bc(g)
+        rp, col = on_device(g)
+        assert rel(gpu.bc_shattered(rp, col, resplit=True).cpu().numpy(), ref) <= TOL64
+        assert rel(gpu.bc_shattered(rp, col, resplit=True, delta_fp32=True).cpu().numpy(), ref) <= TOL32
+        assert rel(gpu.bc_shattered(rp, col, resplit=True, order=True).cpu().numpy(), ref) <= TOL64
+    graphs = RESPLIT_GRAPHS
+    g = gg.disjoint_union(*graphs)
+    off = np.cumsum([0] + [x.n for x in graphs])
+    assert rel(gpu.bc_shattered_batch(off, g.row_ptr, g.col, resplit=True), oracle.bc(g)) <= TOL64
+
+
+@pytest.mark.parametrize("path", LARGE_PATHS)
+def test_resplit_on_a_large_piece(gpu, path, monkeypatch):
+    monkeypatch.setenv("BCS_LARGE_PATH", path)
+    g = gg.with_twins_and_pendants(gg.chung_lu(3000, 2.3, 6, 5), 6, 900, 1500, 100)
+    ref = oracle.bc(g)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, resplit=True), ref) <= TOL64
+    assert gpu.last_stats()["n_large_sources"] > 0
+
+
 # --------------------------------------------------------------- errors
 def test_malformed_inputs_rejected(gpu):
     bad = {
