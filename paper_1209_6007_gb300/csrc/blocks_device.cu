@@ -5,7 +5,8 @@
 //
 // Biconnected components follow Tarjan and Vishkin's characterisation over
 // any rooted spanning tree, here a BFS forest (one tree per component, rooted
-// at its smallest live vertex; every vertex takes its smallest-id neighbour of
+// at its live vertex of largest degree, the smallest id among those; every
+// vertex takes its smallest-id neighbour of
 // the previous level as parent, so the forest is deterministic; the preorder
 // numbers depend on the order of atomics, the blocks do not):
 //   pre[v]  preorder number, nd[v] subtree size,
