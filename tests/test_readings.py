@@ -6,7 +6,9 @@ the CPU against the oracle's plain Brandes (Eq. 1).
 * identical classes whose members differ in reach (Section 3.3.3 leaves
   reach and ident together out);
 * a merged vertex that is a cut vertex (Fig. 3), split with fractional
-  copies.
+  copies;
+* merging again after that split (classes whose members are themselves
+  merged vertices or copies).
 
 Each test writes the reading out with a small weighted Bc-Reach of its own
 (Algorithm 2 with reach and ident: a predecessor v counts ident[v] times in
@@ -251,3 +253,78 @@ def test_merged_cut_vertex_split_with_fractional_copies():
                 bcp[v] += x
         got = np.array([(bcp[w] if v in T else bcp[v]) + extra[v] for v in range(n)])
         assert rel(got, ref) <= 1e-12
+
+
+def test_merging_again_after_the_split():
+    """After the split at the merged twins w, a vertex x whose neighbours are
+    exactly w's in one block becomes identical to w's copy there.  Merged
+    into one vertex U (K = 1 + k members; sub-units {x} and w's k members,
+    weights T_x and T_w, T = T_x + T_w): dependency start T/K - 1, and on
+    each member m of sub-unit i, (t_m - T/K)(N - T) + (t_m - 1)(T - T_i);
+    each common neighbour gets (T^2 - T_x^2 - T_w^2) / K_N.  Pairs inside a
+    sub-unit were counted when it formed, hence T - T_i."""
+    import networkx as nx
+    rng = np.random.default_rng(5)
+    for _ in range(30):
+        na, nb = int(rng.integers(3, 8)), int(rng.integers(3, 8))
+        G = nx.Graph()
+        for off, m in ((0, na), (na, nb)):
+            G.add_edges_from((off + i, off + (i + 1) % m) for i in range(m))
+            for a, b in rng.integers(0, m, (2, 2)):
+                if a != b:
+                    G.add_edge(off + int(a), off + int(b))
+        SA = [int(v) for v in rng.choice(na, 2, replace=False)]
+        SB = [na + int(v) for v in rng.choice(nb, 2, replace=False)]
+        k = int(rng.integers(2, 5))
+        twins = list(range(na + nb, na + nb + k))
+        G.add_edges_from((t, s) for t in twins for s in SA + SB)
+        x = na + nb + k
+        G.add_edges_from((x, s) for s in SA)
+        n = N = G.number_of_nodes()
+        g = gg.from_edges(n, sorted((min(a, b), max(a, b)) for a, b in G.edges()))
+        ref = oracle.bc(g)
+        w = twins[0]
+        bc = np.zeros(n)
+        for s in SA + SB:  # the twins' type-I class terms, reach 1
+            bc[s] += k * (k - 1) / (len(SA) + len(SB))
+        H = G.copy()
+        H.remove_nodes_from(twins[1:])
+        ident = {v: 1 for v in H}
+        ident[w] = k
+        cuts = set(nx.articulation_points(H))
+        merged = 0
+        for blk in map(set, nx.biconnected_components(H)):
+            t = {}
+            for v in blk:
+                other = 0.0
+                if v in cuts:
+                    Hv = H.copy()
+                    Hv.remove_node(v)
+                    other = sum(ident[y] for c in nx.connected_components(Hv) if not (c & blk) for y in c)
+                t[v] = 1.0 + other / ident[v]
+            adj = {v: set(y for y in H[v] if y in blk) for v in blk}
+            if x in blk and w in blk and adj[x] == adj[w]:
+                merged += 1
+                K, Tx, Tw = 1 + k, t[x], k * t[w]
+                T = Tx + Tw
+                nodes = [v for v in blk if v != x]
+                reach = {v: t[v] for v in nodes}
+                reach[w] = T / K
+                idn = {v: ident[v] for v in nodes}
+                idn[w] = K
+                part = weighted_bcreach({v: adj[v] - {x} for v in nodes}, nodes, reach, idn, nodes)
+                for v in nodes:
+                    if v != w:
+                        bc[v] += part[v]
+                bc[x] += part[w] + (t[x] - T / K) * (N - T) + (t[x] - 1) * (T - Tx)
+                for tw in twins:
+                    bc[tw] += part[w] + (t[w] - T / K) * (N - T) + (t[w] - 1) * (T - Tw)
+                for s in adj[x]:
+                    bc[s] += (T * T - Tx * Tx - Tw * Tw) / len(adj[x])
+            else:
+                part = weighted_bcreach(adj, blk, t, ident, blk)
+                for v in blk:
+                    for member in (twins if v == w else [v]):
+                        bc[member] += part[v]
+        assert merged == 1
+        assert rel(bc, ref) <= 1e-12
