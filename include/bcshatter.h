@@ -40,9 +40,12 @@
  * launch and a device-wide synchronisation).
  *
  * Environment: BCS_TRACE (any value) prints per-stage timings to stderr;
- * BCS_LARGE_PATH=batched|per_source forces the kernel used for pieces too
- * large for shared memory (32 sources per CTA, or one), which is otherwise
- * chosen from the number of sources, the memory it needs and the BFS depth.
+ * BCS_LARGE_PATH=wide|batched|per_source forces the kernel used for pieces
+ * too large for shared memory (the whole GPU on one batch of 32 sources, 32
+ * sources per CTA, or one), which is otherwise chosen from the piece's size,
+ * its BFS depth, the number of sources and the memory each kernel needs;
+ * BCS_LARGE_PATH=wide_all (for tests) sends every piece through the
+ * whole-GPU kernel where its depth allows.
  */
 #ifndef BCSHATTER_H
 #define BCSHATTER_H
@@ -139,6 +142,8 @@ typedef struct bcs_stats {
   int64_t small_ng_cap;    /* most sources one small-path CTA ran at once */
   int64_t small_smem_budget; /* shared-memory budget per small-path CTA (bytes) */
   int64_t n_side;          /* side vertices taken out of the pieces (BCS_STEP_S) */
+  int64_t n_wide_batches;  /* 32-source batches run with the whole GPU on one batch
+                              (large pieces of small BFS depth) */
   double work_nm;          /* sum over pieces of n_c * m_c (m_c undirected) */
   double work_sources_entries; /* sum over processed sources of the piece's CSR entries */
   double work_sources_vertices; /* sum over processed sources of the piece's vertices */
@@ -147,7 +152,8 @@ typedef struct bcs_stats {
   double ms_validate;      /* CSR check */
   double ms_cc;            /* connected components */
   double ms_peel;          /* degree-1 removal */
-  double ms_blocks;        /* biconnected split, host side, incl. copies */
+  double ms_blocks;        /* biconnected split (device kernels and the host
+                              steps between them) */
   double ms_ident;         /* identical-vertex merging */
   double ms_plan;          /* work list */
   double ms_bcreach_small; /* Bc-Reach, shared-memory kernel */

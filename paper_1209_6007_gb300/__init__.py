@@ -1,8 +1,8 @@
 """GB300 shattered betweenness centrality: Python binding of libbcshatter.so.
 
 The binding only marshals arguments: every step of the computation runs in
-the library's CUDA kernels (and, for the biconnected split, its host C++
-code).  There is no CPU fallback; a missing library raises.
+the library's CUDA kernels, driven by its host C++ code (planning, launches,
+copies).  There is no CPU fallback; a missing library raises.
 
 Graphs are given as CSR arrays (``row_ptr`` int64[n+1], ``col`` int32[nnz]),
 symmetric, rows strictly ascending, no self-loops.  Pass numpy arrays for

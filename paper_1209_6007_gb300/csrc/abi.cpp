@@ -17,6 +17,11 @@ static thread_local bcs_stats t_stats{};
 static thread_local bool t_stats_valid = false;
 
 void set_error(const std::string &msg) { t_err = msg; }
+
+int64_t &alloc_budget() {
+  static thread_local int64_t budget = -1;
+  return budget;
+}
 const std::string &get_error() { return t_err; }
 
 StageTimer::StageTimer(cudaStream_t stream) : s(stream) {
@@ -131,6 +136,9 @@ int make_ctx(const bcs_opts *opts, Ctx *ctx) {
   const int64_t mw = opts ? opts->max_wait : 0;
   ctx->max_wait = mw == 0 ? DEFAULT_MAX_WAIT : (mw < 0 ? 0 : mw);
   ctx->autotune = opts && opts->autotune;
+  const char *fa = std::getenv("BCS_TEST_FAIL_ALLOC");
+  alloc_budget() = fa ? std::max<int64_t>(0, std::atoll(fa)) : -1;
+  if (const char *sc = std::getenv("BCS_TEST_SIGMA_CAP")) ctx->sigma_cap_lg2 = std::max(1, std::atoi(sc));
   return BCS_OK;
 }
 

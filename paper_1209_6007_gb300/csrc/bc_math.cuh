@@ -99,4 +99,28 @@ __device__ __forceinline__ double recip_pos(double x) {
   return __longlong_as_double(__double_as_longlong(r) - ((long long)(ex - 1023) << 52));
 }
 
+// Per-source 2-bit fields packed in one 64-bit word (32 sources, source i in
+// bits 2i and 2i+1).
+// bit i of x -> bit 2i
+__device__ __forceinline__ uint64_t spread2(uint32_t x) {
+  uint64_t v = x;
+  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+  v = (v | (v << 2)) & 0x3333333333333333ull;
+  v = (v | (v << 1)) & 0x5555555555555555ull;
+  return v;
+}
+
+// bit 2i of v -> bit i
+__device__ __forceinline__ uint32_t compact2(uint64_t v) {
+  v &= 0x5555555555555555ull;
+  v = (v | (v >> 1)) & 0x3333333333333333ull;
+  v = (v | (v >> 2)) & 0x0F0F0F0F0F0F0F0Full;
+  v = (v | (v >> 4)) & 0x00FF00FF00FF00FFull;
+  v = (v | (v >> 8)) & 0x0000FFFF0000FFFFull;
+  v = (v | (v >> 16)) & 0x00000000FFFFFFFFull;
+  return (uint32_t)v;
+}
+
 }  // namespace bcs

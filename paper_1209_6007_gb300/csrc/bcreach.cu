@@ -32,6 +32,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <numeric>
 #include <set>
@@ -50,6 +51,10 @@ constexpr int DISC_CH = 4;  // row entries per step of the shared-memory discove
 constexpr int LARGE_THREADS = 512;
 // BFS depth above which large pieces run one source per CTA rather than 32
 constexpr int MS_DEPTH_LIMIT = 64;
+// Large pieces with at least this many vertices and a BFS eccentricity (from
+// their first vertex) of at most WIDE_MAX_ECC run on the whole-GPU path
+constexpr int WIDE_MIN_N = 32768;
+constexpr int WIDE_MAX_ECC = 40;
 
 struct SmallItem {
   int32_t comp;
@@ -728,16 +733,6 @@ static int launch_large_t(Ctx &ctx, int grid, const LargeSrc *work, int64_t nwor
   return BCS_OK;
 }
 
-#define BCS_DISPATCH3(FN, R, I, F, ...)                             \
-  ((R) ? ((I) ? ((F) ? FN<true, true, true>(__VA_ARGS__)            \
-                     : FN<true, true, false>(__VA_ARGS__))          \
-              : ((F) ? FN<true, false, true>(__VA_ARGS__)           \
-                     : FN<true, false, false>(__VA_ARGS__)))        \
-       : ((I) ? ((F) ? FN<false, true, true>(__VA_ARGS__)           \
-                     : FN<false, true, false>(__VA_ARGS__))         \
-              : ((F) ? FN<false, false, true>(__VA_ARGS__)          \
-                     : FN<false, false, false>(__VA_ARGS__))))
-
 // The small-path work splits the autotuner tries: most sources a CTA runs
 // at once, and the shared-memory budget per CTA (100 KB: 2 CTAs per SM,
 // 72 KB: 3, 54 KB: 4).  The default is the first.
@@ -780,6 +775,10 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     comps_src[0].nsrc = (int32_t)po.nsources;
   }
   const std::vector<CompDesc> &comps = po.sources ? comps_src : comps_in;
+  // BCS_LARGE_PATH=wide_all (tests): every piece runs on the large-piece
+  // path, and on the whole-GPU kernel wherever that can take it
+  const char *lp_env = std::getenv("BCS_LARGE_PATH");
+  const bool all_large = lp_env && !std::strcmp(lp_env, "wide_all");
   std::vector<SmallItem> items;
   std::vector<LargeSrc> work;
   std::vector<int32_t> large, small;
@@ -792,7 +791,8 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     if (ns == 0) continue;
     work_se += (double)ns * (double)c.nnz;
     work_sv += (double)ns * (double)c.n;
-    const bool fits = !po.force_large && !dbg && c.n <= 65535 && small_smem_bytes(c.n, c.nnz, 1, R, I) <= SMALL_SMEM;
+    const bool fits = !po.force_large && !all_large && !dbg && c.n <= 65535 &&
+                      small_smem_bytes(c.n, c.nnz, 1, R, I) <= SMALL_SMEM;
     if (fits) {
       small.push_back((int32_t)ci);
       total_small_cost += (double)ns * (double)(c.nnz + c.n);
@@ -857,6 +857,55 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     grid = (int)std::min<int64_t>(grid, (int64_t)out.size());
     return BCS_OK;
   };
+  // Large pieces of small BFS depth: the whole GPU on one 32-source batch at
+  // a time (wide.cu), the sources taken in the BFS order of the piece from
+  // its first vertex (neighbouring sources share most of their levels).  The
+  // BFS from that vertex also bounds the depth: no source reaches deeper than
+  // twice its eccentricity.  BCS_LARGE_PATH=wide takes every large piece
+  // whose depth allows it; batched|per_source take none.
+  struct WidePiece {
+    int32_t ci;
+    std::shared_ptr<DBuf<int32_t>> order;
+    int32_t nsrc;
+  };
+  std::vector<WidePiece> wide;
+  {
+    const char *lp = std::getenv("BCS_LARGE_PATH");
+    const bool force_wide = lp && (!std::strcmp(lp, "wide") || !std::strcmp(lp, "wide_all"));
+    const bool no_wide = lp && (!std::strcmp(lp, "batched") || !std::strcmp(lp, "per_source"));
+    std::vector<int32_t> rest;
+    for (int32_t ci : large) {
+      const CompDesc &c = comps[ci];
+      const bool cand = !no_wide && !dbg && !po.per_source_large && (c.src_off < 0 || po.sources) &&
+                        (force_wide || c.n >= WIDE_MIN_N);
+      if (!cand) {
+        rest.push_back(ci);
+        continue;
+      }
+      auto ord = std::make_shared<DBuf<int32_t>>();
+      BCS_TRY(ord->alloc(c.n, ctx.stream));
+      int depth = 0;
+      int64_t reached = 0;
+      BCS_TRY(bfs_queue(ctx, in.row + c.row_off, in.col, c.n, 0, ord->p, &depth, &reached));
+      const int limit = force_wide ? wide_depth_limit() : std::min(wide_depth_limit(), WIDE_MAX_ECC);
+      // the depth bound holds within the searched component only
+      if (depth > limit || reached != c.n) {
+        rest.push_back(ci);
+        continue;
+      }
+      int32_t ns = (int32_t)nsrc_of(c);
+      if (po.sources) {  // the caller's sources, in the caller's order
+        std::vector<int32_t> h(po.nsources);
+        for (int64_t i = 0; i < po.nsources; i++) h[i] = (int32_t)po.sources[i];
+        BCS_TRY(ord->alloc(std::max<int64_t>(po.nsources, 1), ctx.stream));
+        BCS_CUDA(cudaMemcpyAsync(ord->p, h.data(), h.size() * sizeof(int32_t), cudaMemcpyHostToDevice, ctx.stream));
+        BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+        ns = (int32_t)po.nsources;
+      }
+      wide.push_back(WidePiece{ci, ord, ns});
+    }
+    large.swap(rest);
+  }
   // Large pieces: 32 sources per CTA when there are enough batches to give
   // every SM two of them and their scratch fits at least one CTA per SM,
   // else one source per CTA (more CTAs in flight).
@@ -933,9 +982,10 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
   ctx.stats.n_small_items = (int64_t)items.size();
   ctx.stats.n_large_sources = 0;
   for (int32_t ci : large) ctx.stats.n_large_sources += nsrc_of(comps[ci]);
+  for (const WidePiece &wp : wide) ctx.stats.n_large_sources += wp.nsrc;
   ctx.stats.work_sources_entries = work_se;
   ctx.stats.work_sources_vertices = work_sv;
-  if (small.empty() && large.empty()) return BCS_OK;
+  if (small.empty() && large.empty() && wide.empty()) return BCS_OK;
 
   DBuf<CompDesc> d_comps;
   DBuf<int> d_err;
@@ -1015,6 +1065,14 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     BCS_TRY(run_small(items, smem_small, grid_small, in.bcp));
     tm.stop_into(ctx, &ctx.stats.ms_bcreach_small);
     tr.mark("small");
+  }
+  for (const WidePiece &wp : wide) {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    BCS_TRY(run_wide(ctx, comps[wp.ci], in, F, wp.order->p, wp.nsrc, d_err.p, d_dag.p));
+    tm.stop_into(ctx, &ctx.stats.ms_bcreach_large);
+    ctx.stats.n_wide_batches += (wp.nsrc + 31) / 32;
+    tr.mark("wide");
   }
   // one source per CTA over the given list; *d_lmax (optional) receives the
   // deepest BFS level any of them reached

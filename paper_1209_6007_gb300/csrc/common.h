@@ -30,11 +30,31 @@ struct Status {
     }                                                                                    \
   } while (0)
 
+// call FN<R, I, F>(...) for runtime flags R, I, F
+#define BCS_DISPATCH3(FN, R, I, F, ...)                             \
+  ((R) ? ((I) ? ((F) ? FN<true, true, true>(__VA_ARGS__)            \
+                     : FN<true, true, false>(__VA_ARGS__))          \
+              : ((F) ? FN<true, false, true>(__VA_ARGS__)           \
+                     : FN<true, false, false>(__VA_ARGS__)))        \
+       : ((I) ? ((F) ? FN<false, true, true>(__VA_ARGS__)           \
+                     : FN<false, true, false>(__VA_ARGS__))         \
+              : ((F) ? FN<false, false, true>(__VA_ARGS__)          \
+                     : FN<false, false, false>(__VA_ARGS__))))
+
 #define BCS_TRY(expr)        \
   do {                       \
     int rc_ = (expr);        \
     if (rc_ != BCS_OK) return rc_; \
   } while (0)
+
+// Test hooks set per call from the environment (host side only; nothing
+// reaches the GPU through them):
+//   BCS_TEST_FAIL_ALLOC=k  the call's device allocations after the first k
+//                          fail as if the device were out of memory;
+//   BCS_TEST_SIGMA_CAP=k   path counts above 2^k count as out of range (the
+//                          whole-GPU Bc-Reach kernel reports BCS_EOVERFLOW).
+// alloc_budget() < 0: no limit.
+int64_t &alloc_budget();
 
 // ------------------------------------------------------- device buffers
 // Stream-ordered device allocation from the device's default memory pool
@@ -61,6 +81,12 @@ struct DBuf {
   }
   int alloc(size_t count, cudaStream_t stream) {
     release();
+    int64_t &budget = alloc_budget();
+    if (budget == 0) {
+      set_error("device allocation refused by BCS_TEST_FAIL_ALLOC");
+      return BCS_ENOMEM;
+    }
+    if (budget > 0) budget--;
     s = stream;
     n = count;
     size_t bytes = (count > 0 ? count : 1) * sizeof(T);
@@ -92,6 +118,9 @@ struct Ctx {
   // spin limit of device-side waits (grid barriers); < 0: give up at once
   int64_t max_wait = 0;
   bool autotune = false;
+  // binary exponent above which a path count counts as out of range
+  // (BCS_TEST_SIGMA_CAP; else effectively unlimited)
+  int sigma_cap_lg2 = 1 << 30;
 };
 
 // Default number of polls (each followed by a short sleep) a device-side
@@ -272,6 +301,19 @@ int run_ms(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32
 // Plan and run Bc-Reach over the given components.  comps are host
 // descriptors; their vertex ranges index BcInput's arrays.
 int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po);
+
+// Bc-Reach over one large piece of small BFS depth with the whole GPU on one
+// 32-source batch at a time (wide.cu).  d_order: the piece's sources (local
+// ids, device), taken 32 at a time in this order.
+int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const int32_t *d_order, int32_t nsrc,
+             int *d_err, unsigned long long *d_dag);
+// deepest BFS level from a root for which run_wide can index every batch
+int wide_depth_limit();
+// BFS of a connected graph from `root` (rows at rp[v]..rp[v+1] of col):
+// queue_out[0..*reached) the vertices in the order the search reaches them,
+// *depth the deepest level (order.cu)
+int bfs_queue(Ctx &ctx, const int64_t *rp, const int32_t *col, int64_t n, int32_t root, int32_t *queue_out,
+              int *depth, int64_t *reached);
 
 // Bc-Reach after one more articulation split of the merged pieces
 // (resplit.cu): in.bcp (the merged vertices' bc') gains the new pieces' bc'.

@@ -55,28 +55,6 @@ struct MsScratch {
   int64_t nmax, qcap;
 };
 
-// bit i of x -> bit 2i
-__device__ __forceinline__ uint64_t spread2(uint32_t x) {
-  uint64_t v = x;
-  v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
-  v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
-  v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
-  v = (v | (v << 2)) & 0x3333333333333333ull;
-  v = (v | (v << 1)) & 0x5555555555555555ull;
-  return v;
-}
-
-// bit 2i of v -> bit i
-__device__ __forceinline__ uint32_t compact2(uint64_t v) {
-  v &= 0x5555555555555555ull;
-  v = (v | (v >> 1)) & 0x3333333333333333ull;
-  v = (v | (v >> 2)) & 0x0F0F0F0F0F0F0F0Full;
-  v = (v | (v >> 4)) & 0x00FF00FF00FF00FFull;
-  v = (v | (v >> 8)) & 0x0000FFFF0000FFFFull;
-  v = (v | (v >> 16)) & 0x00000000FFFFFFFFull;
-  return (uint32_t)v;
-}
-
 // sources whose 2-bit level field equals L mod 4 (reachedness not checked)
 __device__ __forceinline__ uint32_t at_level(uint64_t lv, int L) {
   const uint64_t x = lv ^ (0x5555555555555555ull * (uint64_t)(L & 3));

@@ -235,6 +235,77 @@ int bfs_order_graph(Ctx &ctx, const DevGraph &g, DBuf<int64_t> *rp2, DBuf<int32_
   return BCS_OK;
 }
 
+// level 0 of a search from one root
+__global__ void k_bfs_root(int64_t n, int32_t root, int32_t *level, int32_t *queue, unsigned long long *lcount) {
+  for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+    level[v] = v == root ? 0 : -1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    queue[0] = root;
+    lcount[0] = 1ull;
+  }
+}
+
+int bfs_queue(Ctx &ctx, const int64_t *rp, const int32_t *col, int64_t n, int32_t root, int32_t *queue_out,
+              int *depth, int64_t *reached) {
+  *depth = 0;
+  *reached = n;
+  if (n <= 1) {
+    if (n == 1) BCS_CUDA(cudaMemcpyAsync(queue_out, &root, sizeof(int32_t), cudaMemcpyHostToDevice, ctx.stream));
+    return BCS_OK;
+  }
+  DBuf<int32_t> level;
+  DBuf<unsigned long long> lcount;
+  BCS_TRY(level.alloc(n, ctx.stream));
+  BCS_TRY(lcount.alloc(n + 2, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(lcount.p, 0, (n + 2) * sizeof(unsigned long long), ctx.stream));
+  k_bfs_root<<<grid_of(n, 256, ctx.num_sms * 8), 256, 0, ctx.stream>>>(n, root, level.p, queue_out, lcount.p);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  int per_sm = 0;
+  BCS_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_order_bfs, ORDER_THREADS, 0));
+  if (per_sm < 1) {
+    set_error("the ordering kernel cannot be resident");
+    return BCS_ECUDA;
+  }
+  DBuf<int> err;
+  DBuf<unsigned int> barw;
+  DBuf<int64_t> out;
+  BCS_TRY(err.alloc(1, ctx.stream));
+  BCS_TRY(barw.alloc(2, ctx.stream));
+  BCS_TRY(out.alloc(1, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(barw.p, 0, 2 * sizeof(unsigned int), ctx.stream));
+  GridBarrier gb{barw.p, barw.p + 1, err.p, (long long)ctx.max_wait};
+  int32_t *levelp = level.p, *queuep = queue_out;
+  unsigned long long *lcp = lcount.p;
+  int64_t *outp = out.p;
+  void *args[] = {(void *)&rp, (void *)&col, (void *)&levelp, (void *)&queuep, (void *)&lcp, (void *)&outp,
+                  (void *)&gb};
+  BCS_CUDA(cudaLaunchCooperativeKernel((const void *)k_order_bfs, dim3(ctx.num_sms), dim3(ORDER_THREADS), args, 0,
+                                       ctx.stream));
+  ctx.launches++;
+  // the deepest level: the last non-empty level counter (the first 4,096 are enough to tell a
+  // shallow graph from a deep one)
+  const int64_t nl = std::min<int64_t>(n + 2, 4096);
+  std::vector<unsigned long long> lc(nl);
+  int h_err = 0;
+  int64_t queued = 0;
+  BCS_CUDA(cudaMemcpyAsync(lc.data(), lcount.p, nl * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaMemcpyAsync(&queued, out.p, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  if (h_err & ERR_TIMEOUT) {
+    set_error("a grid-wide wait of the BFS kernel ran out (opts->max_wait)");
+    return BCS_ETIMEOUT;
+  }
+  *reached = queued;
+  int d = 0;
+  for (int64_t l = 0; l < nl; l++)
+    if (lc[l]) d = (int)l;
+  *depth = lc[nl - 1] ? (int)n : d;  // past the counters read: deep
+  return BCS_OK;
+}
+
 __global__ void k_order_map_sources(int64_t k, const int64_t *__restrict__ src, const int32_t *__restrict__ inv,
                                     int64_t *out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
