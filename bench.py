@@ -2,14 +2,22 @@
 
 One step = one bcs_bc_shattered call (validate, connected components,
 degree-1 removal, biconnected split, identical-vertex merging, Bc-Reach over
-all pieces, map-back) on the articulation-heavy workload: 5,000 Erdos-Renyi
-blocks (sizes log-uniform 4-512, mean degree 6) glued at random cut vertices
-plus 20% of the vertices in dangling chains, seeded, FP64 dependencies.
+all pieces, map-back) on one workload, seeded:
+
+* twins (default, the headline): the identical-vertex heavy social-like graph
+  (Chung-Lu core of 500,000 vertices, gamma 2.1, mean degree 12; twin groups
+  of 2-8 covering 150,000 vertices; 350,000 pendants; n = 970,060,
+  m = 5,024,502), the configuration with the most edges, FP32 dependencies
+  as its statement asks;
+* articulation: 5,000 Erdos-Renyi blocks (sizes log-uniform 4-512, mean
+  degree 6) glued at cut vertices plus 20% dangling chains, FP64;
+* road: 1500 x 1500 grid minus 25% of its edges, largest component, trees on
+  10% of the perimeter (n = 2,258,525), FP32 dependencies.
 
 metric: effective GTEPS = n * m / T with n, m of the input graph (sources x
 undirected edges per second, the work plain Brandes would do) and T the
-device time of one step; e2e: the same through host buffers with the
-host<->device copies inside the timed region.
+device time of one step; e2e: the same through host buffers (pinned), with
+the host<->device copies inside the timed region.
 
 --impl reference times the CPU oracle (plain Brandes, FP64) on the host
 cores over a bounded sample of sources of the same graph.
@@ -36,11 +44,20 @@ sys.path.insert(0, ROOT)
 METRIC = "BC GTEPS (sources·m/s), shattered vs plain Brandes on GB300, rel err ≤1e-5"
 L2_BYTES = 129 * 1024 * 1024
 
+# workload -> (config id, FP32 dependencies, description)
+WORKLOADS = {
+    "twins": (3, True, "identical-vertex heavy social-like: Chung-Lu core 500k (gamma 2.1, mean deg 12) + twin "
+                       "groups of 2-8 on 15% of vertices + 350k pendants"),
+    "articulation": (2, False, "articulation-heavy: 5000 ER blocks (log-uniform 4-512, mean deg 6) + 20% chains"),
+    "road": (4, True, "road-like: 1500x1500 grid minus 25% of edges, largest component, trees on 10% of the "
+                      "perimeter"),
+}
+
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=100, help="workload size in percent (100 = full)")
@@ -48,11 +65,11 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="articulation", choices=["articulation", "batch", "side", "unequal"],
-                    help="batch: a secondary measurement of many independent graphs in one call; "
-                         "side: the articulation workload with added side vertices, shattered with and "
-                         "without the side-vertex step; unequal: a twin-heavy graph whose twins carry "
-                         "pendants, with and without merging twins of unequal reach (none is the headline line)")
+    ap.add_argument("--workload", default="twins", choices=list(WORKLOADS) + ["batch", "side", "unequal"],
+                    help="twins (the headline), articulation, road; batch: many independent graphs in one call; "
+                         "side: the articulation workload with added side vertices, shattered with and without "
+                         "the side-vertex step; unequal: a twin-heavy graph whose twins carry pendants, with and "
+                         "without merging twins of unequal reach")
     ap.add_argument("--batch-count", type=int, default=20000)
     ap.add_argument("--batch-nmax", type=int, default=4096)
     return ap.parse_args()
@@ -127,32 +144,38 @@ def max_over_ranks(x: float, world: int) -> float:
     return float(t.item())
 
 
-def workload(scale: int):
+def workload(name: str, scale: int):
     import graphgen as gg
-    g = gg.config(2, scale_pct=scale)
-    return g, {"workload": "articulation-heavy: 5000 ER blocks (log-uniform 4-512, mean deg 6) + 20% chains"
-               if scale == 100 else f"articulation-heavy at {scale}% of its blocks",
-               "n": g.n, "m": g.m, "seed": g.meta["seed"], "delta": "fp64"}
+    cfg_id, fp32, desc = WORKLOADS[name]
+    g = gg.config(cfg_id, scale_pct=scale)
+    return g, {"workload": desc if scale == 100 else f"{desc}, at {scale}% of its size", "n": g.n, "m": g.m,
+               "seed": g.meta["seed"], "delta": "fp32" if fp32 else "fp64"}, fp32
 
 
-KERNEL_SOURCES = ("bcreach.cu", "bc_math.cuh")  # what the Bc-Reach kernels compile from
+# ncu summaries of the dominant kernels, each keyed by the SHA-1 of the
+# sources the kernel compiles from; a figure is used only while they match
+PROFILES = {
+    "small": ("bcreach_small_articulation.json", ("bcreach.cu", "bc_math.cuh")),
+    "wide": ("bcreach_wide_twins.json", ("wide.cu", "bc_math.cuh", "coop.cuh")),
+}
 
 
-def kernel_source_sha1() -> str:
+def kernel_source_sha1(files) -> str:
     import hashlib
     h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
+    for f in files:
         h.update(open(os.path.join(ROOT, "paper_1209_6007_gb300", "csrc", f), "rb").read())
     return h.hexdigest()
 
 
-def measured_traffic():
-    """DRAM bytes per launch of the Bc-Reach kernel from the committed ncu
-    summary, if it was taken on the current kernel sources (else None)."""
+def measured_traffic(kind: str):
+    """The committed ncu summary's record for the kernel, if it was taken on
+    the current kernel sources (else None)."""
+    fname, files = PROFILES[kind]
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "bcreach_small_articulation.json")))
-        if rec.get("source_sha1") == kernel_source_sha1():
-            return float(rec["dram_bytes_per_launch"])
+        rec = json.load(open(os.path.join(ROOT, "profiles", fname)))
+        if rec.get("source_sha1") == kernel_source_sha1(files):
+            return rec
     except (OSError, ValueError, KeyError):
         pass
     return None
@@ -180,7 +203,8 @@ def run_reference(args):
     rank, world, _ = dist_setup(args.gpus)
     if rank != 0:
         return
-    g, cfg = workload(args.scale)
+    name = args.workload if args.workload in WORKLOADS else "twins"
+    g, cfg, _ = workload(name, args.scale)
     import oracle
     cores = oracle.default_threads()
     rng = np.random.default_rng(777)
@@ -204,11 +228,56 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {**cfg, "sample": f"{k} sources per step"},
+            "config": {**cfg, "delta": "fp64", "sample": f"{k} sources per step"},
             "cpu_baseline": {"value": value, "unit": "GTEPS", "cores": cores, "kind": "oracle",
                              "sample": f"{k} seeded sources per step of the full graph"},
             "e2e": {"value": value, "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
+
+
+def roofline(st: dict, clk: dict, peaks: dict, n_sm: int) -> dict:
+    """Roofline of the call's dominant Bc-Reach kernel.
+
+    Large pieces (the whole-GPU kernel): HBM.  Algorithmic bytes per
+    (source, CSR entry) of a piece, with S sources sharing one adjacency
+    read: 8/S (the row) + 2/8 (level bits) + f_DAG * 28 (path count written
+    and read, coefficient, weights, per shortest-path DAG edge) + (n / 2m) *
+    32 (per-vertex state written and read once); f_DAG is the DAG edges the
+    call counted over its (source, entry) pairs.  Per launch: the sum over
+    processed sources of these bytes, over the kernel's CUDA-event time.
+
+    Shared-memory pieces only: the FP64 pipe, as 2 FLOP per DAG edge plus 9
+    per (source, vertex), against 152 SMs x 4 FP64 FLOP/clk at the sampled
+    clock."""
+    dag = float(st["dag_edges"])
+    wse, wsv = float(st["work_sources_entries"]), float(st["work_sources_vertices"])
+    sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
+    if st["ms_bcreach_large"] > st["ms_bcreach_small"]:
+        S = 32
+        f_dag = dag / wse if wse else 0.0
+        by = wse * (8.0 / S + 2.0 / 8.0 + f_dag * 28.0) + wsv * 32.0
+        ms = st["ms_bcreach_large"]
+        peak = float(peaks.get("hbm_gbs", 6800.0))
+        achieved = by / (ms / 1e3) / 1e9
+        rec = measured_traffic("wide")
+        traffic = rec["dram_bytes_per_batch"] * st["n_wide_batches"] if rec and st["n_wide_batches"] else None
+        return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_bcreach_wide (whole GPU on one 32-source batch)",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
+                "work": {"bytes": by, "f_dag": f_dag, "sources_x_entries": wse, "sources_x_vertices": wsv,
+                         "batches": int(st["n_wide_batches"]), "ms": ms,
+                         "traffic_scaled_from": "ncu DRAM bytes of one 32-source batch x batches" if traffic else None}}
+    flop = 2.0 * dag + 9.0 * wsv
+    ms = st["ms_bcreach_small"]
+    fp64_peak = n_sm * 4.0 * sm_mhz * 1e6 / 1e12
+    achieved = flop / (ms / 1e3) / 1e12 if ms > 0 else None
+    rec = measured_traffic("small")
+    return {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": (achieved / fp64_peak) if achieved else None,
+            "traffic": rec["dram_bytes_per_launch"] if rec else None,
+            "kernel": "k_bcreach_small (FP64 dependencies)",
+            "peak_source": f"derived: {n_sm} SMs x 4 FP64 FLOP/clk x {sm_mhz:.0f} MHz (sampled)",
+            "work": {"dag_edges": dag, "source_vertices": wsv, "flop": flop, "ms": ms}}
 
 
 def run_ours(args):
@@ -218,19 +287,18 @@ def run_ours(args):
     torch.cuda.set_device(local)
     import paper_1209_6007_gb300 as bcs
     bcs.load()
-    g, cfg = workload(args.scale)
+    g, cfg, fp32 = workload(args.workload, args.scale)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     rp = torch.from_numpy(g.row_ptr).cuda()
     col = torch.from_numpy(g.col).cuda()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):  # the first call also runs the autotuner
-        bcs.bc_shattered(rp, col, autotune=True)
+        bcs.bc_shattered(rp, col, delta_fp32=fp32, autotune=True)
     torch.cuda.synchronize()
     stage_sum = {}
     launches = 0
@@ -244,7 +312,7 @@ def run_ours(args):
         flush.zero_()  # L2 flush between timed steps (outside the events)
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        bc = bcs.bc_shattered(rp, col, autotune=True)
+        bc = bcs.bc_shattered(rp, col, delta_fp32=fp32, autotune=True)
         ev1.record(stream)
         ev1.synchronize()
         dev_ms += ev0.elapsed_time(ev1)
@@ -263,28 +331,43 @@ def run_ours(args):
     stages = {k: v / args.steps for k, v in stage_sum.items()}
     st = bcs.last_stats()
 
-    # end to end through host buffers
+    # end to end through host buffers in pinned memory
     e2e = None
     if not args.no_e2e:
-        for _ in range(2):
-            bcs.bc_shattered(g.row_ptr, g.col, autotune=True)
+        rp_h = torch.from_numpy(g.row_ptr).pin_memory().numpy()
+        col_h = torch.from_numpy(g.col).pin_memory().numpy()
+        ke = max(1, min(args.steps, 3))
+        bcs.bc_shattered(rp_h, col_h, delta_fp32=fp32, autotune=True)
         te = 0.0
-        for _ in range(args.steps):
+        for _ in range(ke):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            bcs.bc_shattered(g.row_ptr, g.col, autotune=True)
+            bcs.bc_shattered(rp_h, col_h, delta_fp32=fp32, autotune=True)
             te += time.perf_counter() - t0
         te = max_over_ranks(te, world)
-        e2e = {"value": world * nm * args.steps / te / 1e9, "unit": "GTEPS",
+        e2e = {"value": world * nm * ke / te / 1e9, "unit": "GTEPS", "steps": ke,
                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes), "d2h_bytes_per_step": int(g.n * 8)}
 
-    # plain Brandes on a sample of sources (same kernels, no shattering)
+    # the other dependency precision on the same step, and its difference
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b_other = bcs.bc_shattered(rp, col, delta_fp32=not fp32, autotune=True)
+    ev1.record(stream)
+    ev1.synchronize()
+    t_other = ev0.elapsed_time(ev1) / 1e3
+    b32, b64 = (bc, b_other) if fp32 else (b_other, bc)
+    err32 = float((b32 - b64).abs().max() / max(1.0, float(b64.abs().max())))
+    other = {"delta": "fp64" if fp32 else "fp32", "gteps": nm / t_other / 1e9, "ms": 1e3 * t_other,
+             "rel_err_fp32_vs_fp64": err32}
+
+    # plain Brandes on a sample of sources (the same graph, nothing shattered)
     plain = None
     if args.plain_sources > 0:
         rng = np.random.default_rng(99)
         src = rng.choice(g.n, size=min(args.plain_sources, g.n), replace=False)
-        bcs.bc_sources(rp, col, src)
+        bcs.bc_sources(rp, col, src[:64])
         torch.cuda.synchronize()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
@@ -292,56 +375,25 @@ def run_ours(args):
         ev1.record(stream)
         ev1.synchronize()
         tp = ev0.elapsed_time(ev1) / 1e3
-        plain = {"gteps": len(src) * g.m / tp / 1e9, "sources": int(len(src)), "seconds": tp}
+        plain = {"gteps": len(src) * g.m / tp / 1e9, "sources": int(len(src)), "seconds": tp, "delta": "fp64"}
 
-    # fp32-delta variant of the same step
-    fp32 = None
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    bcs.bc_shattered(rp, col, delta_fp32=True, autotune=True)
-    ev0.record(stream)
-    b32 = bcs.bc_shattered(rp, col, delta_fp32=True, autotune=True)
-    ev1.record(stream)
-    ev1.synchronize()
-    t32 = ev0.elapsed_time(ev1) / 1e3
-    ref = bc.double()
-    err32 = float((b32 - ref).abs().max() / max(1.0, float(ref.abs().max())))
-    fp32 = {"gteps": nm / t32 / 1e9, "rel_err_vs_fp64": err32,
-            "speedup_vs_plain_fp64": (nm / t32 / 1e9 / plain["gteps"]) if plain else None}
-
-    # roofline of the dominant kernel (Bc-Reach, shared-memory path): it is
-    # bound by GB300's FP64 pipe, so the figure is algorithmic FP64 FLOP/s:
-    # 2 per shortest-path DAG edge (path-count add, dependency add) and 9 per
-    # (source, vertex) (sigma*ident, the dependency FMA, the coefficient
-    # k(1+delta)/sigma counted as FMA + divide, and the bc FMA).  The peak is
-    # GB300's FP64 rate, 2 FP64 FMA per clock per SM (nominal 1.25 TFLOP/s),
-    # at the SM clock sampled during the timed region.
-    dag = float(st["dag_edges"])
-    vsrc = float(st["work_sources_vertices"])
-    ms_k = st["ms_bcreach_small"] + st["ms_bcreach_large"]
-    flop = 2.0 * dag + 9.0 * vsrc
-    sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = torch.cuda.get_device_properties(local).multi_processor_count
-    fp64_peak = n_sm * 4.0 * sm_mhz * 1e6 / 1e12  # TFLOP/s
-    achieved = flop / (ms_k / 1e3) / 1e12 if ms_k > 0 else None
-    roof = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": (achieved / fp64_peak) if achieved else None, "traffic": measured_traffic(),
-            "kernel": "k_bcreach_small (FP64 dependencies)",
-            "peak_source": f"derived: {n_sm} SMs x 4 FP64 FLOP/clk x {sm_mhz:.0f} MHz (sampled)",
-            "work": {"dag_edges": dag, "source_vertices": vsrc, "flop": flop, "ms": ms_k}}
+    roof = roofline(st, clk, peaks, n_sm)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "GTEPS", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * T / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {**cfg, "l2": "flushed between timed steps (256 MB write)",
-                           "parallelism": f"{world} replica(s)"},
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
+                "config": {**cfg, "precision": ("dependencies FP32; path counts int64, else FP64; bc FP64"
+                                                if fp32 else "dependencies and bc FP64; path counts int64, else FP64"),
+                           "l2": "flushed between timed steps (256 MB write)", "parallelism": f"{world} replica(s)"},
                 "e2e": e2e, "gpu_launches": launches, "clocks": clk, "roofline": roof,
                 "stages_ms": stages, "pieces": int(st["n_pieces"]), "merged_vertices": int(st["n_merged"]),
-                "bfs_levels": int(st["bfs_levels"]),
-                "work_nm_pieces": float(st["work_nm"]), "plain": plain,
-                "speedup_vs_plain": (value / plain["gteps"]) if plain else None, "fp32_delta": fp32,
-                "wall_s": wall}
+                "large_sources": int(st["n_large_sources"]), "wide_batches": int(st["n_wide_batches"]),
+                "bfs_levels": int(st["bfs_levels"]), "work_nm_pieces": float(st["work_nm"]),
+                "raw_gteps": float(st["work_nm"]) * args.steps / (dev_ms / 1e3) / 1e9,
+                "other_delta": other, "plain": plain,
+                "speedup_vs_plain": (value / plain["gteps"]) if plain else None, "wall_s": wall}
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(g, args.cpu_seconds)
         print(json.dumps(line))
@@ -394,7 +446,7 @@ def run_batch(args):
             "gpu_launches": launches, "clocks": clk,
             "stages_ms": {k: v for k, v in st.items() if k.startswith("ms_")},
             "pieces": st["n_pieces"], "large_sources": st["n_large_sources"],
-            "note": "secondary measurement; the headline line is --workload articulation"}
+            "note": "secondary measurement; the headline line is --workload twins"}
     print(json.dumps(line))
 
 
@@ -450,7 +502,7 @@ def run_side(args):
             "gpu_launches": on["launches"], "clocks": on["clocks"], "side_step": on,
             "without_side_step": {**off, "gteps": work / (off["ms"] / 1e3) / 1e9},
             "speedup_of_side_step": off["ms"] / on["ms"],
-            "note": "secondary measurement; the headline line is --workload articulation"}
+            "note": "secondary measurement; the headline line is --workload twins"}
     print(json.dumps(line))
 
 
@@ -509,7 +561,7 @@ def run_unequal(args):
             "gpu_launches": on["launches"], "clocks": on["clocks"], "unequal_reach_classes": on,
             "equal_reach_classes": {**off, "gteps": work / (off["ms"] / 1e3) / 1e9},
             "speedup_of_unequal_classes": off["ms"] / on["ms"], "max_rel_diff_between_the_two": diff,
-            "note": "secondary measurement; the headline line is --workload articulation"}
+            "note": "secondary measurement; the headline line is --workload twins"}
     print(json.dumps(line))
 
 

@@ -867,6 +867,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     int32_t ci;
     std::shared_ptr<DBuf<int32_t>> order;
     int32_t nsrc;
+    int depth_bound;
   };
   std::vector<WidePiece> wide;
   {
@@ -887,9 +888,10 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
       int depth = 0;
       int64_t reached = 0;
       BCS_TRY(bfs_queue(ctx, in.row + c.row_off, in.col, c.n, 0, ord->p, &depth, &reached));
-      const int limit = force_wide ? wide_depth_limit() : std::min(wide_depth_limit(), WIDE_MAX_ECC);
-      // the depth bound holds within the searched component only
-      if (depth > limit || reached != c.n) {
+      // every source's BFS depth is at most twice the root's (the bound holds
+      // within the searched component only)
+      const int bound = 2 * depth + 2;
+      if (bound > wide_depth_limit() || (!force_wide && depth > WIDE_MAX_ECC) || reached != c.n) {
         rest.push_back(ci);
         continue;
       }
@@ -902,7 +904,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
         BCS_CUDA(cudaStreamSynchronize(ctx.stream));
         ns = (int32_t)po.nsources;
       }
-      wide.push_back(WidePiece{ci, ord, ns});
+      wide.push_back(WidePiece{ci, ord, ns, bound});
     }
     large.swap(rest);
   }
@@ -1069,9 +1071,8 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
   for (const WidePiece &wp : wide) {
     StageTimer tm(ctx.stream);
     tm.start();
-    BCS_TRY(run_wide(ctx, comps[wp.ci], in, F, wp.order->p, wp.nsrc, d_err.p, d_dag.p));
+    BCS_TRY(run_wide(ctx, comps[wp.ci], in, F, wp.order->p, wp.nsrc, wp.depth_bound, d_err.p, d_dag.p));
     tm.stop_into(ctx, &ctx.stats.ms_bcreach_large);
-    ctx.stats.n_wide_batches += (wp.nsrc + 31) / 32;
     tr.mark("wide");
   }
   // one source per CTA over the given list; *d_lmax (optional) receives the
@@ -1158,6 +1159,14 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
   if (h_err & ERR_OVERFLOW) {
     set_error("shortest-path counts overflowed the FP64 range within one BFS level");
     return BCS_EOVERFLOW;
+  }
+  if (h_err & ERR_DEPTH) {
+    set_error("a Bc-Reach batch needed more BFS levels than its bound");
+    return BCS_ECUDA;
+  }
+  if (h_err & ERR_TIMEOUT) {
+    set_error("a grid-wide wait of the Bc-Reach kernel ran out (opts->max_wait)");
+    return BCS_ETIMEOUT;
   }
   return BCS_OK;
 }

@@ -305,9 +305,11 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in,
 // Bc-Reach over one large piece of small BFS depth with the whole GPU on one
 // 32-source batch at a time (wide.cu).  d_order: the piece's sources (local
 // ids, device), taken 32 at a time in this order.
+// depth_bound: no source of the piece reaches deeper (at most
+// wide_depth_limit()).
 int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const int32_t *d_order, int32_t nsrc,
-             int *d_err, unsigned long long *d_dag);
-// deepest BFS level from a root for which run_wide can index every batch
+             int depth_bound, int *d_err, unsigned long long *d_dag);
+// deepest BFS level run_wide can index
 int wide_depth_limit();
 // BFS of a connected graph from `root` (rows at rp[v]..rp[v+1] of col):
 // queue_out[0..*reached) the vertices in the order the search reaches them,

@@ -31,11 +31,14 @@ static __device__ bool grid_wait(const GridBarrier &b) {
       atomicAdd(b.gen, 1u);
     } else {
       long long polls = 0;
+      unsigned ns = 32;  // back off between polls so the arriving CTAs' atomics are not crowded out
       while (*(volatile unsigned int *)b.gen == g) {
         if (polls++ >= b.limit || *(volatile int *)b.err) {
           ok = 0;
           break;
         }
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
       }
     }
     __threadfence();

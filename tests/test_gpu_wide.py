@@ -56,15 +56,17 @@ def wide_all(monkeypatch):
     monkeypatch.setenv("BCS_LARGE_PATH", "wide_all")
 
 
-def test_wide_plain_and_repeated_sources(gpu, wide_all):
-    """Plain Brandes on a connected Chung-Lu graph (90 batches of 32), then a
-    source list of 45 entries with repeats (a ragged last batch; equal
-    sources in one batch share one entry)."""
+@pytest.mark.parametrize("per_batch", [32, 64])
+def test_wide_plain_and_repeated_sources(gpu, wide_all, monkeypatch, per_batch):
+    """Plain Brandes on a connected Chung-Lu graph (batches of 32 or 64
+    sources), then a source list of 45 entries with repeats (a ragged last
+    batch; equal sources in one batch are two slots of one vertex)."""
+    monkeypatch.setenv("BCS_WIDE_SOURCES", str(per_batch))
     g = largest_component(gg.chung_lu(3000, 2.2, 8.0, 7))
     ref = oracle.bc(g)
     for fp32, tol in ((False, TOL64), (True, TOL32)):
         assert rel(gpu.bc_plain(g.row_ptr, g.col, delta_fp32=fp32), ref) <= tol
-        assert gpu.last_stats()["n_wide_batches"] == (g.n + 31) // 32
+        assert gpu.last_stats()["n_wide_batches"] == (g.n + per_batch - 1) // per_batch
     src = np.concatenate([np.random.default_rng(1).choice(g.n, 40, replace=False), [5, 5, 9, 9, 0]])
     assert rel(gpu.bc_sources(g.row_ptr, g.col, src), oracle.bc_sources(g, src)) <= TOL64
 
@@ -82,8 +84,8 @@ def test_wide_shattered_reach_and_ident(gpu, wide_all, seed):
 
 def test_wide_split_rows(gpu, wide_all):
     """Hubs of degree above the 256 row entries one warp takes: their rows
-    are split over several warps whose partial sums meet in an accumulator
-    (the five largest hubs among the sources)."""
+    are cut into items spread over several warps (the five largest hubs
+    among the sources)."""
     g = largest_component(gg.chung_lu(20000, 2.0, 12.0, 3))
     deg = np.diff(g.row_ptr)
     assert deg.max() > 512
@@ -95,10 +97,10 @@ def test_wide_split_rows(gpu, wide_all):
 
 
 def test_wide_path_counts_past_int64_and_double(gpu, wide_all):
-    """Layers of 200 vertices (rows of 400 entries, split): path counts grow
-    by 200 per level, leave the 64-bit integers after 8 levels and the
-    double range (200^139 ~ 2^1062) before the last layer."""
-    k, layers = 200, 140
+    """Layers of 400 vertices (rows of 800 entries, split over four warps):
+    path counts grow by 400 per level, leave the 64-bit integers after 7
+    levels and the double range (400^119 ~ 2^1029) before the last layer."""
+    k, layers = 400, 120
     g = layered(k, layers)
     src = np.array([0, 1, 199, 70 * k + 3, k * layers - 1])
     ref = oracle.bc_sources(g, src)
