@@ -228,7 +228,9 @@ int bcs_debug_sssp(const bcs_csr *csr, int64_t s, const bcs_opts *opts, int32_t 
  * 42 MB (64 CTAs x 16,384 vertices), which every GPU that loads this library
  * holds until the process exits.  The first call on a device looks up that
  * array's address (cudaGetSymbolAddress) and may load the library's device
- * code; make that first call before any stream capture.  Every call shares
+ * code; make that first call before any stream capture.  The address is kept
+ * for the life of the process, so resetting the device (cudaDeviceReset)
+ * between calls is not supported.  Every call shares
  * the array and resets the parts that must start cleared, so calls that
  * overlap on the GPU (two streams, two threads) race and must not be issued.
  */

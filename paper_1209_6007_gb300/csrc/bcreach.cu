@@ -888,8 +888,14 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
       int depth = 0;
       int64_t reached = 0;
       BCS_TRY(bfs_queue(ctx, in.row + c.row_off, in.col, c.n, 0, ord->p, &depth, &reached));
-      // every source's BFS depth is at most twice the root's (the bound holds
-      // within the searched component only)
+      if (reached != c.n && c.row_off == 0) {
+        // a whole graph of several components (the plain calls; pieces are
+        // connected): every component searched from its smallest vertex
+        DevGraph g{c.n, c.nnz, in.row, in.col};
+        BCS_TRY(bfs_queue_components(ctx, g, ord->p, &depth));
+        reached = c.n;
+      }
+      // every source's BFS depth is at most twice its component's root's
       const int bound = 2 * depth + 2;
       if (bound > wide_depth_limit() || (!force_wide && depth > WIDE_MAX_ECC) || reached != c.n) {
         rest.push_back(ci);
@@ -1203,6 +1209,10 @@ int launch_plain_fixed_scratch(Ctx &ctx, const int64_t *row, const int32_t *col,
   p += 256;
   int *err = (int *)p;
   p += 256;
+  if (p != scratch + fixed_scratch_arrays_offset(N)) {
+    set_error("fixed scratch layout mismatch");
+    return BCS_ECUDA;
+  }
   LargeScratch sc;
   sc.nmax = (int64_t)N;
   sc.d = (int32_t *)p;

@@ -316,6 +316,9 @@ int wide_depth_limit();
 // *depth the deepest level (order.cu)
 int bfs_queue(Ctx &ctx, const int64_t *rp, const int32_t *col, int64_t n, int32_t root, int32_t *queue_out,
               int *depth, int64_t *reached);
+// BFS order of every connected component of g (rows start at 0), each from
+// its smallest vertex, components contiguous; *depth the deepest level
+int bfs_queue_components(Ctx &ctx, const DevGraph &g, int32_t *queue_out, int *depth);
 
 // Bc-Reach after one more articulation split of the merged pieces
 // (resplit.cu): in.bcp (the merged vertices' bc') gains the new pieces' bc'.
@@ -334,9 +337,15 @@ namespace bcs {
 // `scratch` (fixed_scratch_bytes(nmax, ctas) bytes); allocates nothing.
 constexpr size_t FIXED_WORK_ITEM_BYTES = 8;
 constexpr size_t fixed_up256(size_t x) { return (x + 255) & ~(size_t)255; }
+// Layout of the region, in order: work items (nmax), the component
+// descriptor, the work counter and the error word (256 bytes each), then the
+// per-CTA arrays.  fixed_scratch_arrays_offset(nmax) is where the per-CTA
+// arrays start; the first of them (distances, reset by the launcher) may
+// serve as a one-word flag before the launch.
+constexpr size_t fixed_scratch_arrays_offset(size_t nmax) { return fixed_up256(nmax * FIXED_WORK_ITEM_BYTES) + 3 * 256; }
 constexpr size_t fixed_scratch_bytes(size_t nmax, size_t ctas) {
-  return fixed_up256(nmax * FIXED_WORK_ITEM_BYTES) + 256 /* component */ + 256 /* counter */ + 256 /* err */ +
-         fixed_up256(ctas * nmax * 4) * 2 + fixed_up256(ctas * nmax * 8) * 3 + fixed_up256(ctas * (nmax + 2) * 4) * 2;
+  return fixed_scratch_arrays_offset(nmax) + fixed_up256(ctas * nmax * 4) * 2 + fixed_up256(ctas * nmax * 8) * 3 +
+         fixed_up256(ctas * (nmax + 2) * 4) * 2;
 }
 int launch_plain_fixed_scratch(Ctx &ctx, const int64_t *row, const int32_t *col, int32_t n, double *bc,
                                unsigned char *scratch, int64_t nmax, int ctas, bool fp32);

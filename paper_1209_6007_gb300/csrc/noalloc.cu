@@ -28,7 +28,8 @@ unsigned char *g_addr[MAX_DEVICES] = {};
 }  // namespace
 
 // Device address of the scratch on the current device (looked up once per
-// device, with that device current).
+// device, with that device current, and kept for the life of the process: a
+// device reset, which would move the array, is not supported).
 static int noalloc_scratch(int device, unsigned char **out) {
   if (device < 0 || device >= MAX_DEVICES) {
     set_error("device ordinal out of range for the static scratch table");
@@ -91,8 +92,7 @@ extern "C" __attribute__((visibility("default"))) int bcs_bc_plain_noalloc(const
       // The CSR check needs one int of device memory: it borrows the first
       // word of the per-CTA distance arrays, which the launcher
       // re-initialises right after.
-      const size_t flag_off = fixed_up256(NOALLOC_MAX_N * FIXED_WORK_ITEM_BYTES) + 3 * 256;
-      int *flags = (int *)(scratch + flag_off);
+      int *flags = (int *)(scratch + fixed_scratch_arrays_offset(NOALLOC_MAX_N));
       DevGraph g;
       g.n = csr->n;
       g.nnz = csr->nnz;

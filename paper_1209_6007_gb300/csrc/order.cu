@@ -306,6 +306,76 @@ int bfs_queue(Ctx &ctx, const int64_t *rp, const int32_t *col, int64_t n, int32_
   return BCS_OK;
 }
 
+// BFS order of every connected component at once (each from its smallest
+// vertex), the components kept contiguous: queue_out[0..n), *depth the
+// deepest level over all components.
+int bfs_queue_components(Ctx &ctx, const DevGraph &g, int32_t *queue_out, int *depth) {
+  const int64_t n = g.n;
+  *depth = 0;
+  if (n == 0) return BCS_OK;
+  DBuf<int32_t> label, level;
+  DBuf<int64_t> N;
+  DBuf<unsigned long long> lcount;
+  BCS_TRY(label.alloc(n, ctx.stream));
+  BCS_TRY(N.alloc(n, ctx.stream));
+  BCS_TRY(launch_cc(ctx, g, label.p, N.p));
+  BCS_TRY(level.alloc(n, ctx.stream));
+  BCS_TRY(lcount.alloc(n + 2, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(lcount.p, 0, (n + 2) * sizeof(unsigned long long), ctx.stream));
+  k_order_roots<<<grid_of(n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(n, label.p, level.p, queue_out, lcount.p);
+  ctx.launches++;
+  BCS_CUDA(cudaGetLastError());
+  DBuf<int> err;
+  DBuf<unsigned int> barw;
+  DBuf<int64_t> out;
+  BCS_TRY(err.alloc(1, ctx.stream));
+  BCS_TRY(barw.alloc(2, ctx.stream));
+  BCS_TRY(out.alloc(1, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(err.p, 0, sizeof(int), ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(barw.p, 0, 2 * sizeof(unsigned int), ctx.stream));
+  GridBarrier gb{barw.p, barw.p + 1, err.p, (long long)ctx.max_wait};
+  const int64_t *rpp = g.rp;
+  const int32_t *colp = g.col;
+  int32_t *levelp = level.p, *queuep = queue_out;
+  unsigned long long *lcp = lcount.p;
+  int64_t *outp = out.p;
+  void *args[] = {(void *)&rpp, (void *)&colp, (void *)&levelp, (void *)&queuep, (void *)&lcp, (void *)&outp,
+                  (void *)&gb};
+  BCS_CUDA(cudaLaunchCooperativeKernel((const void *)k_order_bfs, dim3(ctx.num_sms), dim3(ORDER_THREADS), args, 0,
+                                       ctx.stream));
+  ctx.launches++;
+  const int64_t nl = std::min<int64_t>(n + 2, 4096);
+  std::vector<unsigned long long> lc(nl);
+  int h_err = 0;
+  int64_t queued = 0;
+  BCS_CUDA(cudaMemcpyAsync(lc.data(), lcount.p, nl * sizeof(unsigned long long), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaMemcpyAsync(&h_err, err.p, sizeof(int), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaMemcpyAsync(&queued, out.p, sizeof(int64_t), cudaMemcpyDeviceToHost, ctx.stream));
+  BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+  if (h_err & ERR_TIMEOUT) {
+    set_error("a grid-wide wait of the BFS kernel ran out (opts->max_wait)");
+    return BCS_ETIMEOUT;
+  }
+  if (queued != n) {
+    set_error("BFS ordering reached " + std::to_string(queued) + " of " + std::to_string(n) + " vertices");
+    return BCS_ECUDA;
+  }
+  int d = 0;
+  for (int64_t l = 0; l < nl; l++)
+    if (lc[l]) d = (int)l;
+  *depth = lc[nl - 1] ? (int)n : d;
+  // contiguous per component, BFS order inside: stable sort by label
+  DBuf<uint32_t> keys, tk;
+  DBuf<int32_t> tv;
+  BCS_TRY(keys.alloc(n, ctx.stream));
+  BCS_TRY(tk.alloc(n, ctx.stream));
+  BCS_TRY(tv.alloc(n, ctx.stream));
+  k_order_keys<<<grid_of(n, 256, ctx.num_sms * 32), 256, 0, ctx.stream>>>(n, queue_out, label.p, keys.p);
+  ctx.launches++;
+  BCS_TRY(radix_sort_pairs(ctx, keys.p, queue_out, tk.p, tv.p, n, bits_for(n)));
+  return BCS_OK;
+}
+
 __global__ void k_order_map_sources(int64_t k, const int64_t *__restrict__ src, const int32_t *__restrict__ inv,
                                     int64_t *out) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)

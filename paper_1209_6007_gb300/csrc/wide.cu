@@ -54,8 +54,11 @@ namespace bcs {
 
 constexpr int WIDE_THREADS = 256;
 constexpr int WIDE_WARPS = WIDE_THREADS / 32;
-constexpr int WIDE_CH = 256;  // row entries per item of a long row
+constexpr int WIDE_CH = 128;  // row entries per item of a long row
 constexpr int WIDE_GRAB = 2;  // bitmap words (or long-row items) a warp takes at a time
+// The work of a pass is handed out from WIDE_SHARDS counters on separate
+// cache lines (one address would serialise every warp's grab).
+constexpr int WIDE_SHARDS = 8;
 
 struct WideScratch {
   uint8_t *lvl;              // [n][32]
@@ -63,7 +66,7 @@ struct WideScratch {
   double *dsum;              // [n][32]
   uint32_t *bits;            // [lcap][nwords]
   int32_t *flag;             // [lcap + 1] some vertex on the level
-  int32_t *wctr;             // [2 lcap] work handed out in each pass (phase 1, phase 2)
+  int32_t *wctr;             // [2 lcap][WIDE_SHARDS][32] work handed out in each pass (phase 1, phase 2)
   unsigned long long *lmax;  // [lcap][32] largest stored count of (level, source), as bits
   int32_t *kshift;           // [lcap][32] power of two taken off the level's counts when pushed
   int32_t *lkind;            // [lcap + 1] 1: the level's counts are int64
@@ -72,9 +75,13 @@ struct WideScratch {
   const int32_t *hc;         // [*nh] first row entry of the item
   const int32_t *hlist;      // [*nhv] the vertices with long rows
   const int32_t *counts;     // [2]: nh, nhv
+  unsigned long long *trace; // nullable: (tag, time) pairs of the first batches' passes (BCS_TRACE)
   int64_t n, nwords;
   int lcap;
 };
+
+constexpr int WIDE_TRACE_BATCHES = 4;
+constexpr int WIDE_TRACE_CAP = 1024;  // pairs
 
 // float -> double from the bit pattern (integer instructions only; the
 // hardware conversion issues on the FP64 pipe).  Finite inputs.
@@ -154,7 +161,19 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
   const int t_hi = 1000 - flg, t_lo = t_hi - 400;
   unsigned long long dag = 0;
   const int nbatch = (nsrc + SB - 1) / SB;
-  for (int b = 0; b < nbatch; b++) {
+  // trace: thread 0 of CTA 0 stamps the end of each pass of the first batches
+  int tpos = 0;
+  int b = 0;
+  auto mark = [&](unsigned tag) {
+    if (S.trace && b < WIDE_TRACE_BATCHES && gtid == 0 && tpos < WIDE_TRACE_CAP) {
+      unsigned long long t;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+      S.trace[2 * tpos] = ((unsigned long long)b << 32) | tag;
+      S.trace[2 * tpos + 1] = t;
+      tpos++;
+    }
+  };
+  for (b = 0; b < nbatch; b++) {
     int32_t my_src[SPL];
     double ws[SPL];  // the sources' weights reach[s] * ident[s]
 #pragma unroll
@@ -183,6 +202,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       }
     }
     if (!grid_wait(bar)) return;
+    mark(0xF000u);
     // ------------------------------------------------ phase 1
     int L = 0;
     int Y[SPL];  // exponent of level L's stored counts, per source
@@ -284,11 +304,22 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       };
       // work: the items of long rows (the longest work) first, then the
       // bitmap's words (light rows), handed out WIDE_GRAB at a time
-      for (;;) {
-        int w0 = 0;
-        if (lane == 0) w0 = atomicAdd(S.wctr + 2 * L, WIDE_GRAB);
-        w0 = __shfl_sync(0xffffffffu, w0, 0);
-        if (w0 >= S.nwords + nh) break;
+      for (int sh = 0; sh < WIDE_SHARDS;) {
+        const int shard = (int)((gtid >> 5) + sh) % WIDE_SHARDS;
+        int g = 0;
+        if (lane == 0) {  // claim the shard's next grab, unless it is already used up
+          int *ctr = S.wctr + ((size_t)2 * L * WIDE_SHARDS + shard) * 32;
+          const int64_t total = S.nwords + nh;
+          const int lim = (int)((total - (int64_t)shard * WIDE_GRAB + (int64_t)WIDE_SHARDS * WIDE_GRAB - 1) /
+                                ((int64_t)WIDE_SHARDS * WIDE_GRAB));
+          g = *(volatile int *)ctr < lim ? atomicAdd(ctr, 1) : lim;
+        }
+        g = __shfl_sync(0xffffffffu, g, 0);
+        const int64_t w0 = (int64_t)g * WIDE_SHARDS * WIDE_GRAB + (int64_t)shard * WIDE_GRAB;
+        if (w0 >= S.nwords + nh) {
+          sh++;  // this shard is empty: help the next one
+          continue;
+        }
         for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords + nh); wi++) {
           if (wi >= nh) {
             const int64_t wd = wi - nh;
@@ -313,6 +344,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
         if (wmax[q]) atomicMax(S.lmax + (size_t)L * SB + 32 * q + lane, wmax[q]);
       if (__any_sync(0xffffffffu, found) && lane == 0) S.flag[L + 1] = 1;
       if (!grid_wait(bar)) return;
+      mark(0x1000u | (unsigned)L);
 #pragma unroll
       for (int q = 0; q < SPL; q++) Y[q] += k[q];
       L++;
@@ -394,11 +426,22 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
           __syncwarp();
         }
       };
-      for (;;) {
-        int w0 = 0;
-        if (lane == 0) w0 = atomicAdd(S.wctr + 2 * l + 1, WIDE_GRAB);
-        w0 = __shfl_sync(0xffffffffu, w0, 0);
-        if (w0 >= S.nwords + nh) break;
+      for (int sh = 0; sh < WIDE_SHARDS;) {
+        const int shard = (int)((gtid >> 5) + sh) % WIDE_SHARDS;
+        int g = 0;
+        if (lane == 0) {  // claim the shard's next grab, unless it is already used up
+          int *ctr = S.wctr + ((size_t)(2 * l + 1) * WIDE_SHARDS + shard) * 32;
+          const int64_t total = S.nwords + nh;
+          const int lim = (int)((total - (int64_t)shard * WIDE_GRAB + (int64_t)WIDE_SHARDS * WIDE_GRAB - 1) /
+                                ((int64_t)WIDE_SHARDS * WIDE_GRAB));
+          g = *(volatile int *)ctr < lim ? atomicAdd(ctr, 1) : lim;
+        }
+        g = __shfl_sync(0xffffffffu, g, 0);
+        const int64_t w0 = (int64_t)g * WIDE_SHARDS * WIDE_GRAB + (int64_t)shard * WIDE_GRAB;
+        if (w0 >= S.nwords + nh) {
+          sh++;
+          continue;
+        }
         for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords + nh); wi++) {
           if (wi >= nh) {
             const int64_t wd = wi - nh;
@@ -419,6 +462,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
         }
       }
       if (!grid_wait(bar)) return;
+      mark(0x2000u | (unsigned)l);
     }
     // ------------------------------------------------ clear for the next batch
     {
@@ -426,10 +470,10 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       const uint4 ff = make_uint4(0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu);
       for (int64_t i = gtid; i < S.n * (SB / 16); i += nthreads) p[i] = ff;
       for (int64_t i = gtid; i < (int64_t)(Lmax + 2) * S.nwords; i += nthreads) S.bits[i] = 0u;
-      for (int64_t i = gtid; i < (int64_t)(Lmax + 3) * SB; i += nthreads) {
+      for (int64_t i = gtid; i < (int64_t)(Lmax + 3) * max(SB, 2 * WIDE_SHARDS); i += nthreads) {
         if (i < (int64_t)(Lmax + 2) * SB) S.lmax[i] = 0ull;
         if (i < Lmax + 3) S.flag[i] = 0;
-        if (i < 2 * (Lmax + 2)) S.wctr[i] = 0;
+        if (i < 2 * (Lmax + 2) * WIDE_SHARDS) S.wctr[i * 32] = 0;
       }
       for (int64_t i = gtid; i < (int64_t)nhv * SB; i += nthreads) {  // long rows' slots (items shared them)
         const size_t x = (size_t)__ldg(S.hlist + (i / SB)) * SB + (i % SB);
@@ -443,6 +487,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       }
     }
     if (!grid_wait(bar)) return;
+    mark(0xE000u);
   }
   if (dag) atomicAdd(dag_total, dag);
 }
@@ -509,14 +554,19 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
   DBuf<double> sig, dsum;
   DBuf<uint32_t> bits, heavy;
   DBuf<int32_t> flag, wctr, kshift, lkind, hlist, hv, hc, counts;
-  DBuf<unsigned long long> lmax, barw;
+  DBuf<unsigned long long> lmax, barw, trace;
+  const bool tracing = std::getenv("BCS_TRACE") != nullptr;
+  if (tracing) {
+    BCS_TRY(trace.alloc(2 * WIDE_TRACE_CAP, s));
+    BCS_CUDA(cudaMemsetAsync(trace.p, 0, 2 * WIDE_TRACE_CAP * 8, s));
+  }
   BCS_TRY(lvl.alloc(SB * n, s));
   BCS_TRY(sig.alloc(SB * n, s));
   BCS_TRY(dsum.alloc(SB * n, s));
   BCS_TRY(bits.alloc((size_t)lcap * nwords, s));
   BCS_TRY(heavy.alloc(nwords, s));
   BCS_TRY(flag.alloc(lcap + 1, s));
-  BCS_TRY(wctr.alloc(2 * lcap, s));
+  BCS_TRY(wctr.alloc((size_t)2 * lcap * WIDE_SHARDS * 32, s));
   BCS_TRY(kshift.alloc((size_t)lcap * SB, s));
   BCS_TRY(lkind.alloc(lcap + 1, s));
   BCS_TRY(lmax.alloc((size_t)lcap * SB, s));
@@ -531,7 +581,7 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
   BCS_CUDA(cudaMemsetAsync(bits.p, 0, (size_t)lcap * nwords * 4, s));
   BCS_CUDA(cudaMemsetAsync(heavy.p, 0, nwords * 4, s));
   BCS_CUDA(cudaMemsetAsync(flag.p, 0, (lcap + 1) * 4, s));
-  BCS_CUDA(cudaMemsetAsync(wctr.p, 0, 2 * lcap * 4, s));
+  BCS_CUDA(cudaMemsetAsync(wctr.p, 0, (size_t)2 * lcap * WIDE_SHARDS * 32 * 4, s));
   BCS_CUDA(cudaMemsetAsync(lmax.p, 0, (size_t)lcap * SB * 8, s));
   BCS_CUDA(cudaMemsetAsync(counts.p, 0, 8, s));
   BCS_CUDA(cudaMemsetAsync(barw.p, 0, 8, s));
@@ -540,8 +590,8 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
       n, row, heavy.p, hlist.p, hv.p, hc.p, counts.p);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
-  WideScratch S{lvl.p, sig.p, dsum.p, bits.p, flag.p, wctr.p, lmax.p, kshift.p, lkind.p, heavy.p, hv.p, hc.p, hlist.p,
-                counts.p, n, nwords, lcap};
+  WideScratch S{lvl.p,   sig.p,   dsum.p,   bits.p,  flag.p,  wctr.p,    lmax.p, kshift.p, lkind.p, heavy.p,
+                hv.p,    hc.p,    hlist.p,  counts.p, tracing ? trace.p : nullptr, n, nwords, lcap};
   GridBarrier gb{(unsigned int *)barw.p, (unsigned int *)barw.p + 1, d_err, (long long)ctx.max_wait};
   const int32_t *colp = in.col;
   double fan = c.fan;
@@ -557,7 +607,25 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
   int cap = 6;
   if (const char *e = std::getenv("BCS_WIDE_CTAS_PER_SM")) cap = std::max(1, std::atoi(e));
   ctx.stats.n_wide_batches += (nsrc + SB - 1) / SB;
-  return BCS_DISPATCH3(wide_launch_t, R, I, fp32, ctx, spl, cap, args);
+  BCS_TRY(BCS_DISPATCH3(wide_launch_t, R, I, fp32, ctx, spl, cap, args));
+  if (tracing) {  // the first batches' pass times (us) to stderr
+    std::vector<unsigned long long> tr(2 * WIDE_TRACE_CAP);
+    BCS_CUDA(cudaMemcpyAsync(tr.data(), trace.p, tr.size() * 8, cudaMemcpyDeviceToHost, s));
+    BCS_CUDA(cudaStreamSynchronize(s));
+    std::string line;
+    for (int i = 1; i < WIDE_TRACE_CAP && tr[2 * i + 1]; i++) {
+      const unsigned tag = (unsigned)(tr[2 * i] & 0xffffffffu);
+      char buf[64];
+      const char *kind = (tag >> 12) == 1 ? "p1L" : (tag >> 12) == 2 ? "p2L" : (tag >> 12) == 0xE ? "clear" : "setup";
+      std::snprintf(buf, sizeof(buf), " %s%u:%.1f", kind, tag & 0xfffu, (tr[2 * i + 1] - tr[2 * i - 1]) * 1e-3);
+      line += buf;
+      if ((tag >> 12) == 0xE) {
+        std::fprintf(stderr, "[bcs trace] wide batch %llu us:%s\n", tr[2 * i] >> 32, line.c_str());
+        line.clear();
+      }
+    }
+  }
+  return BCS_OK;
 }
 
 }  // namespace bcs

@@ -108,15 +108,17 @@ def test_wide_path_counts_past_int64_and_double(gpu, wide_all):
     assert rel(gpu.bc_sources(g.row_ptr, g.col, src, delta_fp32=True), ref) <= TOL32
 
 
-def test_wide_device_input_and_disconnected_fallback(gpu, wide_all):
-    """Device-resident input gives the same result; a disconnected graph
-    (the depth bound of one search does not cover the other components)
-    takes the other large-piece kernels."""
+def test_wide_device_input_and_several_components(gpu, wide_all):
+    """Device-resident input gives the same result; a whole graph of several
+    components (plain Brandes) is ordered component by component, each from
+    its smallest vertex, so batches may span components."""
     import torch
     g = largest_component(gg.chung_lu(2000, 2.3, 6.0, 11))
     ref = oracle.bc(g)
     rp, col = torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda()
     assert rel(gpu.bc_plain(rp, col).cpu().numpy(), ref) <= TOL64
-    h = gg.disjoint_union(g, gg.cycle(40))
+    h = gg.disjoint_union(gg.cycle(40), g, gg.path(7), gg.star(5), gg.gnp(1, 0.5, 0))
     assert rel(gpu.bc_plain(h.row_ptr, h.col), oracle.bc(h)) <= TOL64
-    assert gpu.last_stats()["n_wide_batches"] == 0
+    assert gpu.last_stats()["n_wide_batches"] > 0
+    src = np.array([0, 39, 40, 41, h.n - 1, h.n - 2, 45])
+    assert rel(gpu.bc_sources(h.row_ptr, h.col, src, delta_fp32=True), oracle.bc_sources(h, src)) <= TOL32

@@ -5,18 +5,22 @@ latency-critical loop that must not enter the CUDA allocator).
 The entry point keeps its kernels' state in one static device array shared
 by every call, so these checks call it twice in a row (and on two different
 graphs) and compare each result with bcs_bc_plain, the allocating entry
-point, within the FP64 tolerance of the other parity tests.  This file is
-collected last so that a failure here stops a -x run only after every other
-test has run.
+point, within the FP64 tolerance of the other parity tests; they also hold
+it to the CPU oracle directly, in both dependency precisions, and on a graph
+of exactly the largest size it accepts (every CTA's slice of the array used
+to its end).  This file is collected last so that a failure here stops a -x
+run only after every other test has run.
 """
 import numpy as np
 import pytest
 
 import graphgen as gg
+import oracle
 
 pytestmark = pytest.mark.gpu
 
 TOL64 = 1e-12
+TOL32 = 1e-5
 
 
 def rel(a, b):
@@ -61,3 +65,22 @@ def test_noalloc_rejects_what_it_cannot_hold(gpu):
     with pytest.raises(TypeError):
         gpu.bc_plain_noalloc(big.row_ptr, big.col)  # host arrays: nothing to copy into
     assert torch.cuda.is_available()
+
+
+def test_noalloc_matches_the_oracle_fp64_and_fp32(gpu):
+    g = gg.config(1)
+    ref = oracle.bc(g)
+    rp, col = dev(g)
+    assert rel(gpu.bc_plain_noalloc(rp, col).cpu().numpy(), ref) <= TOL64
+    assert rel(gpu.bc_plain_noalloc(rp, col, delta_fp32=True).cpu().numpy(), ref) <= TOL32
+    assert rel(gpu.bc_plain_noalloc(rp, col).cpu().numpy(), ref) <= TOL64  # FP64 again after FP32
+
+
+def test_noalloc_at_the_largest_size(gpu):
+    """A 128 x 128 grid: exactly NOALLOC_MAX_N vertices."""
+    g = gg.grid(128, 128)
+    assert g.n == gpu.NOALLOC_MAX_N
+    ref = oracle.bc(g)
+    rp, col = dev(g)
+    for _ in range(2):
+        assert rel(gpu.bc_plain_noalloc(rp, col).cpu().numpy(), ref) <= TOL64
