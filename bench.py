@@ -65,11 +65,13 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="twins", choices=list(WORKLOADS) + ["batch", "side", "unequal"],
+    ap.add_argument("--workload", default="twins",
+                    choices=list(WORKLOADS) + ["batch", "side", "unequal", "twins-batch"],
                     help="twins (the headline), articulation, road; batch: many independent graphs in one call; "
                          "side: the articulation workload with added side vertices, shattered with and without "
                          "the side-vertex step; unequal: a twin-heavy graph whose twins carry pendants, with and "
-                         "without merging twins of unequal reach")
+                         "without merging twins of unequal reach; twins-batch: one 64-source batch of the "
+                         "twin workload's largest piece through the whole-GPU kernel, run twice (for profilers)")
     ap.add_argument("--batch-count", type=int, default=20000)
     ap.add_argument("--batch-nmax", type=int, default=4096)
     return ap.parse_args()
@@ -253,7 +255,8 @@ def roofline(st: dict, clk: dict, peaks: dict, n_sm: int) -> dict:
     wse, wsv = float(st["work_sources_entries"]), float(st["work_sources_vertices"])
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
     if st["ms_bcreach_large"] > st["ms_bcreach_small"]:
-        S = 32
+        # sources sharing one batch of the whole-GPU kernel (32 or 64)
+        S = 64 if st["n_wide_batches"] and st["n_large_sources"] > 32 * st["n_wide_batches"] else 32
         f_dag = dag / wse if wse else 0.0
         by = wse * (8.0 / S + 2.0 / 8.0 + f_dag * 28.0) + wsv * 32.0
         ms = st["ms_bcreach_large"]
@@ -262,7 +265,7 @@ def roofline(st: dict, clk: dict, peaks: dict, n_sm: int) -> dict:
         rec = measured_traffic("wide")
         traffic = rec["dram_bytes_per_batch"] * st["n_wide_batches"] if rec and st["n_wide_batches"] else None
         return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_bcreach_wide (whole GPU on one 32-source batch)",
+                "traffic": traffic, "kernel": f"k_bcreach_wide (whole GPU on one {S}-source batch)",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
                 "work": {"bytes": by, "f_dag": f_dag, "sources_x_entries": wse, "sources_x_vertices": wsv,
                          "batches": int(st["n_wide_batches"]), "ms": ms,
@@ -350,6 +353,10 @@ def run_ours(args):
                "h2d_bytes_per_step": int(g.row_ptr.nbytes + g.col.nbytes), "d2h_bytes_per_step": int(g.n * 8)}
 
     # the other dependency precision on the same step, and its difference
+    # (shared-memory workloads: one untimed call first, which runs that
+    # precision's autotuner; a large piece's call is too long to repeat)
+    if float(st["ms_bcreach_large"]) < 1000.0:
+        bcs.bc_shattered(rp, col, delta_fp32=not fp32, autotune=True)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
@@ -565,6 +572,36 @@ def run_unequal(args):
     print(json.dumps(line))
 
 
+def run_twins_batch(args):
+    """One 64-source batch of the twin workload's largest piece (after
+    shattering: 423,691 vertices, 5,781,604 entries) through the whole-GPU
+    Bc-Reach kernel, FP32 dependencies, run twice; the sources are spread
+    over the piece (ids i * 7919 mod n).  A small, fixed launch for ncu."""
+    import torch
+    import graphgen as gg
+    import paper_1209_6007_gb300 as bcs
+    torch.cuda.set_device(0)
+    bcs.load()
+    g = gg.config(3, scale_pct=args.scale)
+    c = bcs.shatter(g.row_ptr, g.col)
+    sizes = np.diff(c.piece_vtx_off)
+    p = int(np.argmax(sizes))
+    a, b = int(c.piece_vtx_off[p]), int(c.piece_vtx_off[p + 1])
+    rp = (c.row_ptr[a:b + 1] - c.row_ptr[a]).astype(np.int64)
+    col = c.col[c.row_ptr[a]:c.row_ptr[b]].astype(np.int32)
+    rows = np.repeat(np.arange(b - a), np.diff(rp))
+    col = col[np.lexsort((col, rows))]  # the piece's rows in ascending order, as the ABI takes them
+    src = (np.arange(64, dtype=np.int64) * 7919) % (b - a)
+    rpd, cold = torch.from_numpy(rp).cuda(), torch.from_numpy(col).cuda()
+    ms = []
+    for _ in range(2):
+        bcs.bc_sources(rpd, cold, src, delta_fp32=True)
+        st = bcs.last_stats()
+        ms.append(st["ms_bcreach_large"])
+    print(json.dumps({"workload": "one 64-source batch of the twin workload's largest piece", "n": int(b - a),
+                      "nnz": int(col.size), "wide_batches": int(st["n_wide_batches"]), "ms_bcreach_large": ms}))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -575,6 +612,8 @@ def main():
         run_side(args)
     elif args.workload == "unequal":
         run_unequal(args)
+    elif args.workload == "twins-batch":
+        run_twins_batch(args)
     else:
         run_ours(args)
 
