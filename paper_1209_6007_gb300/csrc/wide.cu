@@ -105,9 +105,11 @@ __device__ __forceinline__ int warp_max_int(int x) {
 // The level bytes of up to 32 neighbours (S per neighbour, one neighbour per
 // lane), moved through shared memory so that lane s can read the bytes of
 // its own sources in every row.
+// A row of the tile is padded by 16 bytes so that the 16-byte stores of
+// eight consecutive lanes fall on distinct banks.
 template <int SPL>
 struct NbrTile {
-  uint4 lv[32][2 * SPL];
+  uint4 lv[32][2 * SPL + 1];
   uint32_t off[32];  // u * S: the neighbour's first slot
 };
 
@@ -128,6 +130,39 @@ __device__ __forceinline__ int32_t load_tile(NbrTile<SPL> &t, const int32_t *__r
   return u;
 }
 
+// The work of a pass (long-row items, then bitmap words) is handed out
+// WIDE_GRAB units at a time from WIDE_SHARDS counters, shard h owning the
+// grabs starting at h * WIDE_GRAB, (h + WIDE_SHARDS) * WIDE_GRAB, ...  Returns
+// the first unit of the warp's next grab, or -1 once every shard is used up
+// (warp-collective).  A warp stays on its shard until it is used up, then
+// reads all the counters at once and moves to the next shard with work left;
+// every failed claim follows another warp's successful one, so the loop ends.
+__device__ __forceinline__ int shard_grabs(int64_t total, int h) {
+  return (int)((total - (int64_t)h * WIDE_GRAB + (int64_t)WIDE_SHARDS * WIDE_GRAB - 1) /
+               ((int64_t)WIDE_SHARDS * WIDE_GRAB));
+}
+
+__device__ __forceinline__ int64_t wide_grab(int32_t *ctrs, int64_t total, int &shard, int lane) {
+  for (;;) {
+    int g = 0;
+    if (lane == 0) {  // claim the shard's next grab, unless it is already used up
+      int32_t *ctr = ctrs + shard * 32;
+      const int lim = shard_grabs(total, shard);
+      g = *(volatile int32_t *)ctr < lim ? atomicAdd(ctr, 1) : lim;
+    }
+    g = __shfl_sync(0xffffffffu, g, 0);
+    const int64_t w0 = (int64_t)g * WIDE_SHARDS * WIDE_GRAB + (int64_t)shard * WIDE_GRAB;
+    if (w0 < total) return w0;
+    bool left = false;
+    if (lane < WIDE_SHARDS) left = *(volatile int32_t *)(ctrs + lane * 32) < shard_grabs(total, lane);
+    const unsigned bm = __ballot_sync(0xffffffffu, left);
+    if (!bm) return -1;
+    // bit i of rot: shard (shard + 1 + i) mod WIDE_SHARDS has work left
+    const unsigned rot = (bm | (bm << WIDE_SHARDS)) >> (shard + 1);
+    shard = (shard + __ffs(rot)) % WIDE_SHARDS;
+  }
+}
+
 template <int SPL>
 __device__ __forceinline__ uint32_t tile_byte(const NbrTile<SPL> &t, int j, int s) {
   return ((const uint8_t *)&t.lv[j][0])[s];
@@ -142,6 +177,8 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
     int32_t nsrc, double *bcp, WideScratch S, GridBarrier bar, int *err, unsigned long long *dag_total, int sig_cap) {
   constexpr int SB = 32 * SPL;  // sources per batch
   __shared__ NbrTile<SPL> s_tile[WIDE_WARPS];
+  __shared__ int32_t s_src[SB];  // the batch's sources (-1 past the end of the list)
+  __shared__ double s_ws[SB];    // their weights reach[s] * ident[s]
   const int lane = threadIdx.x & 31;
   NbrTile<SPL> &tile = s_tile[threadIdx.x >> 5];
   const int64_t gtid = (int64_t)blockIdx.x * WIDE_THREADS + threadIdx.x;
@@ -174,22 +211,23 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
     }
   };
   for (b = 0; b < nbatch; b++) {
-    int32_t my_src[SPL];
-    double ws[SPL];  // the sources' weights reach[s] * ident[s]
-#pragma unroll
-    for (int q = 0; q < SPL; q++) {
-      const int64_t i = (int64_t)SB * b + 32 * q + lane;
-      my_src[q] = i < nsrc ? __ldg(order + i) : -1;
-      ws[q] = 0.0;
-      if (my_src[q] >= 0)
-        ws[q] = (REACH ? (init_f ? __ldg(init_f + my_src[q]) + 1.0 : (double)__ldg(reach + my_src[q])) : 1.0) *
-                (IDENT ? (double)__ldg(ident + my_src[q]) : 1.0);
+    // every CTA keeps the batch's sources and weights in shared memory (the
+    // previous batch's last use of them ended at a grid-wide wait)
+    if (threadIdx.x < SB) {
+      const int64_t i = (int64_t)SB * b + threadIdx.x;
+      const int32_t sv = i < nsrc ? __ldg(order + i) : -1;
+      s_src[threadIdx.x] = sv;
+      s_ws[threadIdx.x] =
+          sv < 0 ? 0.0
+                 : (REACH ? (init_f ? __ldg(init_f + sv) + 1.0 : (double)__ldg(reach + sv)) : 1.0) *
+                       (IDENT ? (double)__ldg(ident + sv) : 1.0);
     }
     // ------------------------------------------------ level 0: the sources
     if (leader) {
 #pragma unroll
       for (int q = 0; q < SPL; q++) {
-        const int32_t sv = my_src[q];
+        const int64_t i = (int64_t)SB * b + 32 * q + lane;
+        const int32_t sv = i < nsrc ? __ldg(order + i) : -1;
         if (sv >= 0) {  // a repeated source is simply two slots of one vertex
           S.lvl[(size_t)sv * SB + 32 * q + lane] = 0;
           sigi[(size_t)sv * SB + 32 * q + lane] = 1;
@@ -218,7 +256,6 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       // the power of two its pushes drop, and level L+1's
       const int kind = __ldcg(S.lkind + L);
       int k[SPL], bexp_max = 0;
-      double kscale[SPL];
 #pragma unroll
       for (int q = 0; q < SPL; q++) {
         int bexp = 0;  // level L's stored counts are below 2^bexp
@@ -231,7 +268,6 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
           bexp = ep + 1 - kp + flg;
         }
         k[q] = (!kind && bexp > t_hi) ? bexp - t_lo : 0;
-        kscale[q] = pow2_int(-k[q]);
         bexp_max = max(bexp_max, bexp);
         if (bexp - k[q] + Y[q] > sig_cap && gtid < 32) atomicOr(err, ERR_OVERFLOW);
         if (leader) S.kshift[(size_t)L * SB + 32 * q + lane] = k[q];
@@ -247,28 +283,29 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       // one vertex (its whole row, or one item of a long row)
       auto visit = [&](int32_t v, int64_t e0, int64_t e1) {
         bool on[SPL];
-        long long pi[SPL];
-        double pd[SPL];
+        // the value pushed for each source: int64 bits when level L+1's
+        // counts are integers, else the bits of a double
+        unsigned long long pv[SPL];
         const long long idv = (IDENT && L > 0) ? (long long)__ldg(ident + v) : 1ll;
         bool any = false;
 #pragma unroll
         for (int q = 0; q < SPL; q++) {
           const size_t x = (size_t)v * SB + 32 * q + lane;
           on[q] = __ldcg(S.lvl + x) == (uint8_t)L;
-          pi[q] = 0;
-          pd[q] = 0.0;
+          pv[q] = 0ull;
           if (on[q]) {
             if (kind) {
               const long long r = __ldcg(sigi + x);
               wmax[q] = (unsigned long long)r > wmax[q] ? (unsigned long long)r : wmax[q];
-              if (kind_next) pi[q] = r * idv;
-              else pd[q] = i64_to_f64_pos(r) * (double)idv;
+              pv[q] = kind_next ? (unsigned long long)(r * idv)
+                                : (unsigned long long)__double_as_longlong(i64_to_f64_pos(r) * (double)idv);
             } else {
               const double r = __ldcg(S.sig + x);
               const unsigned long long rb = (unsigned long long)__double_as_longlong(r);
               wmax[q] = rb > wmax[q] ? rb : wmax[q];
-              pd[q] = r * kscale[q];
-              if (IDENT && L > 0) pd[q] *= (double)idv;
+              double p = r * pow2_int(-k[q]);
+              if (IDENT && L > 0) p *= (double)idv;
+              pv[q] = (unsigned long long)__double_as_longlong(p);
             }
           }
           any |= on[q];
@@ -290,8 +327,8 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
                   lvl_l[off] = (uint8_t)nextl;
                   fr |= 1u << j;
                 }
-                if (kind_next) atomicAdd(sigu_l + off, (unsigned long long)pi[q]);
-                else atomicAdd(sigd_l + off, pd[q]);
+                if (kind_next) atomicAdd(sigu_l + off, pv[q]);
+                else atomicAdd(sigd_l + off, __longlong_as_double((long long)pv[q]));
               }
             }
           }
@@ -304,22 +341,10 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       };
       // work: the items of long rows (the longest work) first, then the
       // bitmap's words (light rows), handed out WIDE_GRAB at a time
-      for (int sh = 0; sh < WIDE_SHARDS;) {
-        const int shard = (int)((gtid >> 5) + sh) % WIDE_SHARDS;
-        int g = 0;
-        if (lane == 0) {  // claim the shard's next grab, unless it is already used up
-          int *ctr = S.wctr + ((size_t)2 * L * WIDE_SHARDS + shard) * 32;
-          const int64_t total = S.nwords + nh;
-          const int lim = (int)((total - (int64_t)shard * WIDE_GRAB + (int64_t)WIDE_SHARDS * WIDE_GRAB - 1) /
-                                ((int64_t)WIDE_SHARDS * WIDE_GRAB));
-          g = *(volatile int *)ctr < lim ? atomicAdd(ctr, 1) : lim;
-        }
-        g = __shfl_sync(0xffffffffu, g, 0);
-        const int64_t w0 = (int64_t)g * WIDE_SHARDS * WIDE_GRAB + (int64_t)shard * WIDE_GRAB;
-        if (w0 >= S.nwords + nh) {
-          sh++;  // this shard is empty: help the next one
-          continue;
-        }
+      int shard = (int)((gtid >> 5) % WIDE_SHARDS);
+      for (;;) {
+        const int64_t w0 = wide_grab(S.wctr + (size_t)2 * L * WIDE_SHARDS * 32, S.nwords + nh, shard, lane);
+        if (w0 < 0) break;
         for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords + nh); wi++) {
           if (wi >= nh) {
             const int64_t wd = wi - nh;
@@ -379,7 +404,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
               const double dv = fma(sv, ds * pow2_int(-kl[q]), init);
               const double kv = IDENT ? (double)__ldg(ident + v) : 1.0;
               cpush[q] = fma(kv, dv, kv) * recip_pos(sv);
-              if (v != my_src[q]) contrib64 = fma(ws[q], dv, contrib64);
+              if (v != s_src[32 * q + lane]) contrib64 = fma(s_ws[32 * q + lane], dv, contrib64);
             } else {
               int ev, ed = 0;
               float mv, md = 0.0f;
@@ -390,7 +415,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
               const float kv = IDENT ? (float)__ldg(ident + v) : 1.0f;
               const float cm = fmaf(kv, df, kv) / mv;  // c[v] = cm * 2^-ev in stored units
               cpush[q] = __longlong_as_double(__double_as_longlong(f32_to_f64_bits(cm)) - ((long long)ev << 52));
-              if (v != my_src[q]) contrib32 = fmaf((float)ws[q], df, contrib32);
+              if (v != s_src[32 * q + lane]) contrib32 = fmaf((float)s_ws[32 * q + lane], df, contrib32);
             }
             if (light) {  // the slots are finished: clear them for the next batch
               S.sig[x] = 0.0;
@@ -426,22 +451,10 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
           __syncwarp();
         }
       };
-      for (int sh = 0; sh < WIDE_SHARDS;) {
-        const int shard = (int)((gtid >> 5) + sh) % WIDE_SHARDS;
-        int g = 0;
-        if (lane == 0) {  // claim the shard's next grab, unless it is already used up
-          int *ctr = S.wctr + ((size_t)(2 * l + 1) * WIDE_SHARDS + shard) * 32;
-          const int64_t total = S.nwords + nh;
-          const int lim = (int)((total - (int64_t)shard * WIDE_GRAB + (int64_t)WIDE_SHARDS * WIDE_GRAB - 1) /
-                                ((int64_t)WIDE_SHARDS * WIDE_GRAB));
-          g = *(volatile int *)ctr < lim ? atomicAdd(ctr, 1) : lim;
-        }
-        g = __shfl_sync(0xffffffffu, g, 0);
-        const int64_t w0 = (int64_t)g * WIDE_SHARDS * WIDE_GRAB + (int64_t)shard * WIDE_GRAB;
-        if (w0 >= S.nwords + nh) {
-          sh++;
-          continue;
-        }
+      int shard = (int)((gtid >> 5) % WIDE_SHARDS);
+      for (;;) {
+        const int64_t w0 = wide_grab(S.wctr + (size_t)(2 * l + 1) * WIDE_SHARDS * 32, S.nwords + nh, shard, lane);
+        if (w0 < 0) break;
         for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords + nh); wi++) {
           if (wi >= nh) {
             const int64_t wd = wi - nh;
@@ -483,7 +496,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       if (leader) {  // level 0
 #pragma unroll
         for (int q = 0; q < SPL; q++)
-          if (my_src[q] >= 0) sigi[(size_t)my_src[q] * SB + 32 * q + lane] = 0;
+          if (s_src[32 * q + lane] >= 0) sigi[(size_t)s_src[32 * q + lane] * SB + 32 * q + lane] = 0;
       }
     }
     if (!grid_wait(bar)) return;
