@@ -278,6 +278,30 @@ def with_side_vertices(base: Graph, seed: int, n_tri: int, n_grow: int = 0) -> G
     return from_edges(n, edges, f"{base.name}+side{n_tri}+grow{n_grow}")
 
 
+def blow_up(base: Graph, seed: int, max_k: int = 3, p_closed: float = 0.3, n_pend: int = 0) -> Graph:
+    """Replace every vertex x of `base` by a group of 1..max_k copies (open
+    twins, or with probability p_closed a clique of closed twins); copies of
+    adjacent vertices are all joined.  Groups of groups collapse in turn once
+    merged, so the result needs several rounds of splitting and merging.
+    n_pend pendants are then attached to uniform vertices."""
+    rng = np.random.default_rng(seed)
+    groups, n = [], 0
+    edges = set()
+    for _ in range(base.n):
+        k = int(rng.integers(1, max_k + 1))
+        grp = list(range(n, n + k))
+        n += k
+        if k > 1 and rng.random() < p_closed:
+            edges.update((a, b) for i, a in enumerate(grp) for b in grp[i + 1:])
+        groups.append(grp)
+    for u, v in base.edges():
+        edges.update((min(a, b), max(a, b)) for a in groups[int(u)] for b in groups[int(v)])
+    for _ in range(n_pend):
+        edges.add((int(rng.integers(0, n)), n))
+        n += 1
+    return from_edges(n, sorted(edges), f"blowup({base.name},{seed},{max_k})+p{n_pend}")
+
+
 def disjoint_union(*graphs: Graph) -> Graph:
     e, off = [], 0
     for g in graphs:

@@ -328,3 +328,130 @@ def test_merging_again_after_the_split():
                         bc[member] += part[v]
         assert merged == 1
         assert rel(bc, ref) <= 1e-12
+
+
+def fixpoint_bc(g):
+    """The preprocessing loop repeated to a fixpoint (Section 3.4, Fig. 3),
+    written out on the CPU.  Every connected component starts as one piece
+    whose vertices are units: k original members of weight t each (T = k t;
+    at first k = t = 1).  A round splits every piece at its cut vertices (a
+    copy weighs T plus all the weight beyond it away from its block, shared
+    by its k members) and merges the identical units of every block.  A class
+    of sub-units x (K = sum k_x, T = sum T_x) becomes one unit of K members of
+    weight T / K; each member of x gets (t_x - T/K)(N - T) + (t_x - 1)(T - T_x)
+    (pairs inside a sub-unit were counted when it formed); in a type-I class
+    (open neighbourhoods equal) every member of a neighbour gets
+    (T^2 - sum T_x^2) / K_N, K_N the members of the class's neighbours.
+    Rounds repeat until one merges nothing; weighted Bc-Reach on the final
+    pieces completes bc.  Returns (bc, rounds)."""
+    import networkx as nx
+    G = nx.Graph()
+    G.add_nodes_from(range(g.n))
+    G.add_edges_from(map(tuple, g.edges()))
+    bc = np.zeros(g.n)
+    members, weight = {}, {}  # unit -> its original vertices; unit -> t
+
+    def unit(mem, t):
+        u = len(members)
+        members[u], weight[u] = mem, t
+        return u
+
+    pieces = []
+    for comp in nx.connected_components(G):
+        ids = {v: unit([v], 1.0) for v in comp}
+        pieces.append((nx.relabel_nodes(G.subgraph(comp), ids), len(comp)))
+    rounds = 0
+    while True:
+        rounds += 1
+        blocks = []
+        for H, N in pieces:
+            if H.number_of_nodes() < 2:
+                continue
+            W = {v: len(members[v]) * weight[v] for v in H}
+            cuts = set(nx.articulation_points(H))
+            for blk in map(set, nx.biconnected_components(H)):
+                copy = {}
+                for v in blk:
+                    beyond = 0.0
+                    if v in cuts:
+                        Hv = H.copy()
+                        Hv.remove_node(v)
+                        beyond = sum(W[y] for c in nx.connected_components(Hv) if not (c & blk) for y in c)
+                    copy[v] = unit(members[v], (W[v] + beyond) / len(members[v]))
+                blocks.append((nx.relabel_nodes(H.subgraph(blk), copy), N))
+        merged_any = False
+        pieces = []
+        for B, N in blocks:
+            by_open, by_closed = {}, {}
+            for v in B:
+                by_open.setdefault(frozenset(B[v]), []).append(v)
+            classes = [(c, True) for c in by_open.values() if len(c) > 1]
+            taken = {v for c, _ in classes for v in c}
+            for v in B:
+                if v not in taken:
+                    by_closed.setdefault(frozenset(B[v]) | {v}, []).append(v)
+            classes += [(c, False) for c in by_closed.values() if len(c) > 1]
+            rename = {}
+            for cls, open_twins in classes:
+                merged_any = True
+                K = sum(len(members[x]) for x in cls)
+                Tx = {x: len(members[x]) * weight[x] for x in cls}
+                T = sum(Tx.values())
+                for x in cls:
+                    amt = (weight[x] - T / K) * (N - T) + (weight[x] - 1.0) * (T - Tx[x])
+                    for m in members[x]:
+                        bc[m] += amt
+                if open_twins:
+                    nbrs = B[cls[0]]
+                    KN = sum(len(members[y]) for y in nbrs)
+                    amt = (T * T - sum(t * t for t in Tx.values())) / KN
+                    for y in nbrs:
+                        for m in members[y]:
+                            bc[m] += amt
+                u = unit([m for x in cls for m in members[x]], T / K)
+                for x in cls:
+                    rename[x] = u
+            if rename:
+                Bm = nx.Graph()
+                Bm.add_nodes_from({rename.get(v, v) for v in B})
+                Bm.add_edges_from((rename.get(a, a), rename.get(b, b)) for a, b in B.edges()
+                                  if rename.get(a, a) != rename.get(b, b))
+                B = Bm
+            pieces.append((B, N))
+        if not merged_any:
+            break
+    for H, N in pieces:
+        nodes = list(H)
+        reach = {v: weight[v] for v in nodes}
+        ident = {v: len(members[v]) for v in nodes}
+        part = weighted_bcreach({v: set(H[v]) for v in nodes}, nodes, reach, ident, nodes)
+        for v in nodes:
+            for m in members[v]:
+                bc[m] += part[v]
+    return bc, rounds
+
+
+def test_preprocessing_loop_to_a_fixpoint_matches_the_oracle():
+    """Blown-up graphs (every vertex of a small base replaced by open or
+    closed twins, pendants added): merged groups become cut vertices, their
+    copies become twins of other groups, and so on, for several rounds."""
+    rounds_seen = []
+    for seed in range(40):
+        rng = np.random.default_rng(100 + seed)
+        nb = int(rng.integers(3, 8))
+        base = gg.random_tree(nb, seed) if seed % 2 else gg.gnp(nb, 0.5, seed)
+        g = gg.blow_up(base, seed, max_k=3, p_closed=0.3, n_pend=int(rng.integers(0, 4)))
+        got, rounds = fixpoint_bc(g)
+        rounds_seen.append(rounds)
+        assert rel(got, oracle.bc(g)) <= 1e-12, (seed, rounds)
+    assert max(rounds_seen) >= 3
+
+
+def test_fixpoint_loop_on_a_nested_four_cycle():
+    """C4 with every vertex blown up: the opposite corners are open twins;
+    merged, the other two corners become twins of each other, then the
+    last edge is a closed pair (three rounds, one vertex left)."""
+    g = gg.blow_up(gg.cycle(4), 3, max_k=3, p_closed=0.0)
+    got, rounds = fixpoint_bc(g)
+    assert rounds >= 3
+    assert rel(got, oracle.bc(g)) <= 1e-12
