@@ -92,14 +92,18 @@ extern "C" {
  * Taken by bcs_bc_shattered and bcs_bc_shattered_batch; not combinable with
  * BCS_STEP_S (BCS_EINVAL). */
 #define BCS_STEP_U 32u
-/* One more articulation split after identical merging (the preprocessing of
- * Section 3.4 repeated once; merging can leave a merged vertex as a cut
- * vertex, Fig. 3), opt-in and not part of BCS_STEPS_ALL: the merged pieces
- * are split into biconnected blocks again, with each merged vertex weighing
- * reach * ident and a cut copy of a vertex standing for k members carrying
- * 1/k of the weight beyond it per member.  The result is the same bc.  Taken
- * by bcs_bc_shattered and bcs_bc_shattered_batch; not combinable with
- * BCS_STEP_S or BCS_STEP_U (BCS_EINVAL). */
+/* The preprocessing of Section 3.4 repeated to a fixpoint (merging can leave
+ * a merged vertex as a cut vertex, Fig. 3, and splitting there can make
+ * copies identical to other vertices), opt-in and not part of BCS_STEPS_ALL:
+ * the merged pieces are split into biconnected blocks again, each merged
+ * vertex weighing reach * ident and a cut copy of a vertex standing for k
+ * members carrying 1/k of the weight beyond it per member; with BCS_STEP_I
+ * the blocks' identical vertices are merged again (classes keyed on the
+ * neighbourhood alone, each copy a sub-unit of k members), and split and
+ * merge repeat until a round merges nothing (at most 64 rounds; every
+ * round's pieces give the same bc).  The result is the same bc.  Taken by
+ * bcs_bc_shattered and bcs_bc_shattered_batch; combinable with BCS_STEP_U,
+ * not with BCS_STEP_S (BCS_EINVAL). */
 #define BCS_STEP_L 64u
 
 typedef struct bcs_csr {
@@ -114,9 +118,14 @@ typedef struct bcs_opts {
   uint32_t steps;     /* BCS_STEP_* mask for bcs_bc_shattered / bcs_shatter */
   int32_t delta_fp32; /* 1: dependency recurrence (Eq. 3) in FP32; path counts
                          and the bc sums stay FP64 */
-  int32_t autotune;   /* 1: pick the shared-memory Bc-Reach work split (how
-                         many sources a CTA runs at once) by timing the
-                         candidates once per shape bucket, then reuse it */
+  int32_t autotune;   /* 1: pick by timing the candidates once per shape
+                         bucket, then reuse the choice: the shared-memory
+                         Bc-Reach work split (how many sources a CTA runs at
+                         once), the small/large threshold (the shared memory
+                         a piece may need to take the small path), and the
+                         kernel of each large piece with many sources
+                         (whole-GPU, 32-source batches or one source per
+                         CTA, each timed on a sample of its sources) */
   int32_t device;     /* CUDA device ordinal; -1 = the current device */
   void *stream;       /* cudaStream_t for all device work; NULL = default */
   int64_t max_wait;   /* polls a device-side wait (grid barrier) makes before
@@ -142,8 +151,16 @@ typedef struct bcs_stats {
   int64_t small_ng_cap;    /* most sources one small-path CTA ran at once */
   int64_t small_smem_budget; /* shared-memory budget per small-path CTA (bytes) */
   int64_t n_side;          /* side vertices taken out of the pieces (BCS_STEP_S) */
-  int64_t n_wide_batches;  /* 32-source batches run with the whole GPU on one batch
-                              (large pieces of small BFS depth) */
+  int64_t n_wide_batches;  /* source batches (64, or 32) run with the whole GPU on
+                              one batch (large pieces of small BFS depth) */
+  int64_t n_rounds;        /* split-and-merge rounds of the preprocessing loop
+                              (BCS_STEP_L) */
+  int64_t small_limit;     /* shared memory (bytes) a piece may need for one source
+                              to take the small path: fixed, or the autotuner's */
+  int64_t tuned;           /* the autotuner's choices this call, as bits: 1 the
+                              small/large threshold; 1 << k a large piece on
+                              kernel k (1 whole-GPU, 2 32-source batches, 3 one
+                              source per CTA) */
   double work_nm;          /* sum over pieces of n_c * m_c (m_c undirected) */
   double work_sources_entries; /* sum over processed sources of the piece's CSR entries */
   double work_sources_vertices; /* sum over processed sources of the piece's vertices */

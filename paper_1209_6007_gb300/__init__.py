@@ -98,11 +98,14 @@ def _csr_of(graph_or_rp, col=None):
     return graph_or_rp, col
 
 
-def bc_plain(row_ptr, col=None, *, delta_fp32: bool = False, stream=None, order: bool = False):
+def bc_plain(row_ptr, col=None, *, delta_fp32: bool = False, stream=None, order: bool = False,
+             autotune: bool = False):
     """Plain Brandes (Algorithm 1) on the whole graph: bc[v] for every v.
-    order=True renumbers the graph in BFS order first (Section 4.1)."""
+    order=True renumbers the graph in BFS order first (Section 4.1);
+    autotune=True times the large-piece kernels once per shape bucket."""
     rp, cl = _csr_of(row_ptr, col)
-    a = _Args(rp, cl, steps=STEPS_ALL | (STEP_O if order else 0), delta_fp32=delta_fp32, stream=stream)
+    a = _Args(rp, cl, steps=STEPS_ALL | (STEP_O if order else 0), delta_fp32=delta_fp32, stream=stream,
+              autotune=autotune)
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_plain(ctypes.byref(a.csr), ctypes.byref(a.opts), ptr))
     return out
@@ -119,7 +122,8 @@ def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool 
     fastest.  order=True renumbers the graph in BFS order first (Section 4.1).
     side=True also takes side vertices out of the pieces (Section 3.3.2).
     unequal=True merges identical vertices whatever their reach.
-    resplit=True splits the merged pieces at their cut vertices once more."""
+    resplit=True repeats the preprocessing to a fixpoint: split the merged
+    pieces at their cut vertices, merge again, until a round merges nothing."""
     rp, cl = _csr_of(row_ptr, col)
     extra = (STEP_O if order else 0) | (STEP_S if side else 0) | (STEP_U if unequal else 0) | \
         (STEP_L if resplit else 0)
@@ -136,7 +140,7 @@ def bc_shattered_batch(vtx_off, row_ptr, col=None, *, steps: int = STEPS_ALL, de
     vertices [vtx_off[g], vtx_off[g+1]); no edge may join two graphs).
     side=True also takes side vertices out of the pieces (Section 3.3.2);
     unequal=True merges identical vertices whatever their reach; resplit=True
-    splits the merged pieces at their cut vertices once more."""
+    repeats splitting and merging until a round merges nothing."""
     rp, cl = _csr_of(row_ptr, col)
     extra = (STEP_S if side else 0) | (STEP_U if unequal else 0) | (STEP_L if resplit else 0)
     a = _Args(rp, cl, steps=steps | extra, delta_fp32=delta_fp32, stream=stream)

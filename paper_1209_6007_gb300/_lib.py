@@ -38,7 +38,7 @@ class Stats(ctypes.Structure):
     _fields_ = [(name, c_i64) for name in (
         "n_pieces", "n_slots", "n_merged", "n_entries", "peel_rounds", "n_small_items",
         "n_large_sources", "kernel_launches", "bfs_levels", "dag_edges", "n_ms_batches", "batch_ctas", "small_ng_cap", "small_smem_budget", "n_side",
-        "n_wide_batches")] + [(name, c_dbl) for name in (
+        "n_wide_batches", "n_rounds", "small_limit", "tuned")] + [(name, c_dbl) for name in (
         "work_nm", "work_sources_entries", "work_sources_vertices", "ms_total", "ms_upload", "ms_validate", "ms_cc", "ms_peel",
         "ms_blocks", "ms_ident", "ms_plan", "ms_bcreach_small", "ms_bcreach_large", "ms_mapback",
         "ms_download", "ms_side")]

@@ -442,10 +442,11 @@ static int with_bfs_order(Ctx &ctx, const bcs_csr *h, double *bc_out, F &&run) {
 
 }  // namespace bcs
 
-// steps S, U and L each change the pieces Bc-Reach runs on; at most one
+// step S (side vertices) takes integer target weights: not with U or L,
+// whose weights are fractional; U and L go together (the loop's merges are
+// of unequal weight anyway)
 static bool optional_steps_compatible(uint32_t steps) {
-  const int k = ((steps & BCS_STEP_S) != 0) + ((steps & BCS_STEP_U) != 0) + ((steps & BCS_STEP_L) != 0);
-  return k <= 1;
+  return !((steps & BCS_STEP_S) && (steps & (BCS_STEP_U | BCS_STEP_L)));
 }
 
 // ================================================================ C ABI
@@ -519,7 +520,7 @@ __attribute__((visibility("default"))) int bcs_bc_shattered(const bcs_csr *csr, 
     return BCS_EINVAL;
   }
   if (opts && !optional_steps_compatible(opts->steps)) {
-    set_error("at most one of BCS_STEP_S, BCS_STEP_U and BCS_STEP_L");
+    set_error("BCS_STEP_S does not combine with BCS_STEP_U or BCS_STEP_L");
     return BCS_EINVAL;
   }
   return guarded(opts, [&](Ctx &ctx) {

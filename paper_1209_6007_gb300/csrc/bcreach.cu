@@ -758,6 +758,114 @@ static void remember_split(long long key, int choice) {
   g_tune[key] = choice;
 }
 
+// Besides the small-path work split, the autotuner picks, by timing each
+// candidate once per shape bucket and caching the fastest:
+//  * the small/large threshold: the shared memory a piece may need for one
+//    source to take the small path (SMALL_LIMITS); pieces above it take the
+//    large-piece path.  Timed over the pieces that fit the largest limit.
+//  * the kernel of each large piece: the whole-GPU kernel (where the
+//    piece's depth allows it), 32-source batches (where its depth is below
+//    4 x MS_DEPTH_LIMIT: their cost grows with the levels of a batch), or
+//    one source per CTA, each timed on a sample of the piece's sources that
+//    fills the GPU for that kernel.
+// Every candidate runs into a scratch accumulator; the call then runs with
+// the choice.  Without the autotuner the fixed limits above decide.
+static const size_t SMALL_LIMITS[] = {SMALL_SMEM, 64 * 1024, 40 * 1024};
+static std::map<long long, int> g_tune_limit, g_tune_large;
+
+static int tuned_in(std::map<long long, int> &m, long long key) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = m.find(key);
+  return it == m.end() ? 0 : it->second;
+}
+
+static void remember_in(std::map<long long, int> &m, long long key, int v) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  m[key] = v;
+}
+
+static long long bits_of(double x) { return x < 1.0 ? 0 : (long long)std::log2(x) + 1; }
+
+// One Bc-Reach run over `comps` into a scratch accumulator, timed; the
+// call's statistics are left as they were.
+static int time_candidate(Ctx &ctx, const std::vector<CompDesc> &comps, const BcInput &in, const BcPlanOpts &po,
+                          double *ms) {
+  int64_t ntot = 1;
+  for (const CompDesc &c : comps) ntot = std::max<int64_t>(ntot, c.vtx_off + c.n);
+  DBuf<double> scratch;
+  BCS_TRY(scratch.alloc(ntot, ctx.stream));
+  BCS_CUDA(cudaMemsetAsync(scratch.p, 0, ntot * sizeof(double), ctx.stream));
+  BcInput in2 = in;
+  in2.bcp = scratch.p;
+  const bool at = ctx.autotune;
+  const bcs_stats saved = ctx.stats;
+  const size_t npend = ctx.pending.size();
+  ctx.autotune = false;
+  StageTimer t(ctx.stream);
+  t.start();
+  const int rc = run_bcreach(ctx, comps, in2, po);
+  *ms = t.stop_ms();
+  ctx.autotune = at;
+  ctx.stats = saved;
+  for (size_t i = npend; i < ctx.pending.size(); i++) {  // the candidate's stage times are not the call's
+    cudaEventSynchronize(ctx.pending[i].b);
+    cudaEventDestroy(ctx.pending[i].a);
+    cudaEventDestroy(ctx.pending[i].b);
+  }
+  ctx.pending.resize(npend);
+  return rc;
+}
+
+// Times the large-piece kernels on samples of one piece's sources (every
+// vertex a source) and sets *choice to the fastest per source.  The samples
+// are what each kernel sees in a full run: consecutive vertices of the BFS
+// order from the piece's first vertex (d_ord) for the whole-GPU kernel,
+// consecutive ids for the others.
+static int tune_large_piece(Ctx &ctx, const CompDesc &c, const BcInput &in, const BcPlanOpts &po, bool wide_ok,
+                            int depth, const int32_t *d_ord, int *choice) {
+  struct Cand {
+    int path;
+    int64_t m;
+  };
+  const int64_t ns = nsrc_of(c), sms = ctx.num_sms;
+  std::vector<Cand> cands;
+  if (wide_ok) cands.push_back({LARGE_PATH_WIDE, 128});
+  if (depth <= 4 * MS_DEPTH_LIMIT) cands.push_back({LARGE_PATH_BATCHED, 32 * sms});
+  cands.push_back({LARGE_PATH_PER_SOURCE, 6 * sms});
+  *choice = cands[0].path;
+  if (cands.size() == 1) return BCS_OK;
+  double best = 0.0;
+  for (const Cand &cd : cands) {
+    const int64_t m = std::min(cd.m, std::max<int64_t>(1, ns / 4));
+    const int64_t at = (ns - m) / 2;
+    std::vector<int64_t> src(m);
+    if (cd.path == LARGE_PATH_WIDE) {
+      std::vector<int32_t> h(m);
+      BCS_CUDA(cudaMemcpyAsync(h.data(), d_ord + at, m * sizeof(int32_t), cudaMemcpyDeviceToHost, ctx.stream));
+      BCS_CUDA(cudaStreamSynchronize(ctx.stream));
+      for (int64_t i = 0; i < m; i++) src[i] = h[i];
+    } else {
+      for (int64_t i = 0; i < m; i++) src[i] = at + i;
+    }
+    BcPlanOpts p2 = po;
+    p2.sources = src.data();
+    p2.nsources = m;
+    p2.large_path = cd.path;
+    p2.force_large = true;
+    double ms = 0.0;
+    BCS_TRY(time_candidate(ctx, std::vector<CompDesc>{c}, in, p2, &ms));
+    const double rate = (double)m / std::max(ms, 1e-3);
+    if (std::getenv("BCS_TRACE"))
+      std::fprintf(stderr, "[bcs] tune large piece n=%d kernel %d: %lld sources in %.3f ms\n", c.n, cd.path,
+                   (long long)m, ms);
+    if (rate > best) {
+      best = rate;
+      *choice = cd.path;
+    }
+  }
+  return BCS_OK;
+}
+
 int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &in, const BcPlanOpts &po) {
   Tracer tr("bcreach", ctx.stream);
   const bool R = in.reach != nullptr || in.init != nullptr, I = in.ident != nullptr, F = po.fp32_delta;
@@ -775,10 +883,58 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     comps_src[0].nsrc = (int32_t)po.nsources;
   }
   const std::vector<CompDesc> &comps = po.sources ? comps_src : comps_in;
-  // BCS_LARGE_PATH=wide_all (tests): every piece runs on the large-piece
-  // path, and on the whole-GPU kernel wherever that can take it
-  const char *lp_env = std::getenv("BCS_LARGE_PATH");
-  const bool all_large = lp_env && !std::strcmp(lp_env, "wide_all");
+  // the large-piece kernel, if fixed: by the caller, or by BCS_LARGE_PATH
+  // (wide|batched|per_source; wide_all, for tests: every piece runs on the
+  // large-piece path, and on the whole-GPU kernel wherever that can take it)
+  int lp_mode = po.large_path;
+  bool all_large = false;
+  if (const char *e = std::getenv("BCS_LARGE_PATH")) {
+    if (!std::strcmp(e, "wide_all")) all_large = true;
+    if (!std::strcmp(e, "wide") || all_large) lp_mode = LARGE_PATH_WIDE;
+    if (!std::strcmp(e, "batched")) lp_mode = LARGE_PATH_BATCHED;
+    if (!std::strcmp(e, "per_source")) lp_mode = LARGE_PATH_PER_SOURCE;
+  }
+  const bool tune = ctx.autotune && lp_mode == LARGE_PATH_AUTO && !dbg && !po.sources && !po.srcmap &&
+                    !po.force_large && !po.per_source_large;
+  // the small/large threshold
+  size_t small_limit = po.small_limit ? po.small_limit : SMALL_SMEM;
+  if (tune && !po.small_limit) {
+    std::vector<CompDesc> elig;  // pieces that fit the largest limit
+    double cost = 0.0, band = 0.0;
+    const size_t lowest = SMALL_LIMITS[sizeof(SMALL_LIMITS) / sizeof(SMALL_LIMITS[0]) - 1];
+    for (const CompDesc &c : comps) {
+      const int64_t ns = nsrc_of(c);
+      if (c.n < 2 || ns == 0 || c.n > 65535) continue;
+      const size_t s1 = small_smem_bytes(c.n, c.nnz, 1, R, I);
+      if (s1 > SMALL_SMEM) continue;
+      elig.push_back(c);
+      cost += (double)ns * (double)(c.nnz + c.n);
+      if (s1 > lowest) band += (double)ns * (double)(c.nnz + c.n);
+    }
+    if (band > 0.0) {
+      const long long key = ((long long)(R * 2 + I) << 40) | (bits_of(cost) << 20) | bits_of(band);
+      int ch = tuned_in(g_tune_limit, key);
+      if (!ch) {
+        double best = 1e300;
+        for (int k = 0; k < (int)(sizeof(SMALL_LIMITS) / sizeof(SMALL_LIMITS[0])); k++) {
+          BcPlanOpts p2 = po;
+          p2.small_limit = SMALL_LIMITS[k];
+          double ms = 0.0;
+          BCS_TRY(time_candidate(ctx, elig, in, p2, &ms));
+          if (std::getenv("BCS_TRACE"))
+            std::fprintf(stderr, "[bcs] tune small/large threshold %zu B: %.3f ms\n", SMALL_LIMITS[k], ms);
+          if (ms < best) {
+            best = ms;
+            ch = k + 1;
+          }
+        }
+        remember_in(g_tune_limit, key, ch);
+      }
+      small_limit = SMALL_LIMITS[ch - 1];
+      ctx.stats.tuned |= 1;
+    }
+  }
+  ctx.stats.small_limit = (int64_t)small_limit;
   std::vector<SmallItem> items;
   std::vector<LargeSrc> work;
   std::vector<int32_t> large, small;
@@ -792,7 +948,7 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     work_se += (double)ns * (double)c.nnz;
     work_sv += (double)ns * (double)c.n;
     const bool fits = !po.force_large && !all_large && !dbg && c.n <= 65535 &&
-                      small_smem_bytes(c.n, c.nnz, 1, R, I) <= SMALL_SMEM;
+                      small_smem_bytes(c.n, c.nnz, 1, R, I) <= small_limit;
     if (fits) {
       small.push_back((int32_t)ci);
       total_small_cost += (double)ns * (double)(c.nnz + c.n);
@@ -870,15 +1026,18 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     int depth_bound;
   };
   std::vector<WidePiece> wide;
+  // large pieces the autotuner gave to 32-source batches, or to one source per CTA
+  std::vector<int32_t> ms_tuned, ps_tuned;
   {
-    const char *lp = std::getenv("BCS_LARGE_PATH");
-    const bool force_wide = lp && (!std::strcmp(lp, "wide") || !std::strcmp(lp, "wide_all"));
-    const bool no_wide = lp && (!std::strcmp(lp, "batched") || !std::strcmp(lp, "per_source"));
+    const bool force_wide = lp_mode == LARGE_PATH_WIDE;
+    const bool no_wide = lp_mode == LARGE_PATH_BATCHED || lp_mode == LARGE_PATH_PER_SOURCE;
     std::vector<int32_t> rest;
     for (int32_t ci : large) {
       const CompDesc &c = comps[ci];
+      // tuning pays only over many sources
+      const bool tune_this = tune && c.src_off < 0 && nsrc_of(c) >= 24LL * ctx.num_sms;
       const bool cand = !no_wide && !dbg && !po.per_source_large && (c.src_off < 0 || po.sources) &&
-                        (force_wide || c.n >= WIDE_MIN_N);
+                        (force_wide || tune_this || c.n >= WIDE_MIN_N);
       if (!cand) {
         rest.push_back(ci);
         continue;
@@ -897,7 +1056,23 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
       }
       // every source's BFS depth is at most twice its component's root's
       const int bound = 2 * depth + 2;
-      if (bound > wide_depth_limit() || (!force_wide && depth > WIDE_MAX_ECC) || reached != c.n) {
+      const bool wide_ok = bound <= wide_depth_limit() && reached == c.n;
+      int choice = LARGE_PATH_AUTO;
+      if (tune_this) {
+        const long long key = ((long long)(R * 2 + I) << 40) | (bits_of(c.n) << 24) |
+                              (bits_of((double)c.nnz / c.n) << 16) | bits_of(depth);
+        choice = tuned_in(g_tune_large, key);
+        if (!choice) {
+          BCS_TRY(tune_large_piece(ctx, c, in, po, wide_ok, depth, ord->p, &choice));
+          remember_in(g_tune_large, key, choice);
+        }
+        ctx.stats.tuned |= 1ll << choice;
+        if (choice == LARGE_PATH_BATCHED) ms_tuned.push_back(ci);
+        if (choice == LARGE_PATH_PER_SOURCE) ps_tuned.push_back(ci);
+        if (choice != LARGE_PATH_WIDE) continue;
+      }
+      const bool heuristic = !force_wide && choice == LARGE_PATH_AUTO;
+      if (!wide_ok || (heuristic && (depth > WIDE_MAX_ECC || c.n < WIDE_MIN_N))) {
         rest.push_back(ci);
         continue;
       }
@@ -928,14 +1103,12 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     BCS_TRY(ms_ctas_that_fit(nmax_large, &fit));
     if (fit < ctx.num_sms) use_ms = false;
   }
-  bool forced = false;  // BCS_LARGE_PATH=batched|per_source overrides the choice
+  bool forced = false;  // a fixed large path (BCS_LARGE_PATH, or the caller's) overrides the choice
   if (!large.empty() && !dbg && !po.per_source_large && !po.srcmap) {
-    if (const char *e = std::getenv("BCS_LARGE_PATH")) {
-      if (!std::strcmp(e, "batched")) use_ms = forced = true;
-      if (!std::strcmp(e, "per_source")) {
-        use_ms = false;
-        forced = true;
-      }
+    if (lp_mode == LARGE_PATH_BATCHED) use_ms = forced = true;
+    if (lp_mode == LARGE_PATH_PER_SOURCE) {
+      use_ms = false;
+      forced = true;
     }
   }
   // the one-source-per-CTA list for large pieces, from the `skip`-th source
@@ -990,10 +1163,12 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
   ctx.stats.n_small_items = (int64_t)items.size();
   ctx.stats.n_large_sources = 0;
   for (int32_t ci : large) ctx.stats.n_large_sources += nsrc_of(comps[ci]);
+  for (int32_t ci : ms_tuned) ctx.stats.n_large_sources += nsrc_of(comps[ci]);
+  for (int32_t ci : ps_tuned) ctx.stats.n_large_sources += nsrc_of(comps[ci]);
   for (const WidePiece &wp : wide) ctx.stats.n_large_sources += wp.nsrc;
   ctx.stats.work_sources_entries = work_se;
   ctx.stats.work_sources_vertices = work_sv;
-  if (small.empty() && large.empty() && wide.empty()) return BCS_OK;
+  if (small.empty() && large.empty() && wide.empty() && ms_tuned.empty() && ps_tuned.empty()) return BCS_OK;
 
   DBuf<CompDesc> d_comps;
   DBuf<int> d_err;
@@ -1155,6 +1330,17 @@ int run_bcreach(Ctx &ctx, const std::vector<CompDesc> &comps_in, const BcInput &
     if (depth_failed) build_work(skip);
     tm.stop_into(ctx, &ctx.stats.ms_bcreach_large);
   }
+  // the pieces the autotuner placed (every vertex a source)
+  if (!ms_tuned.empty()) {
+    StageTimer tm(ctx.stream);
+    tm.start();
+    bool depth_failed = false;
+    BCS_TRY(run_ms(ctx, comps, ms_tuned, in, F, nullptr, 0, 0, d_comps.p, d_err.p, d_dag.p, &depth_failed));
+    if (depth_failed) ps_tuned.insert(ps_tuned.end(), ms_tuned.begin(), ms_tuned.end());
+    tm.stop_into(ctx, &ctx.stats.ms_bcreach_large);
+  }
+  for (int32_t ci : ps_tuned)
+    for (int32_t i = 0; i < comps[ci].n; i++) work.push_back(LargeSrc{ci, i});
   if (!work.empty()) BCS_TRY(run_per_source(work, nullptr));
   int h_err = 0;
   unsigned long long h_dag = 0;

@@ -215,8 +215,10 @@ struct DevMerged {
 };
 
 // identical: merge identical vertices; unequal: key classes on the
-// neighbourhood alone (members may differ in reach)
-int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerged *out);
+// neighbourhood alone (members may differ in reach); sub_k (nullable, with
+// unequal): slot x stands for sub_k[x] members whose weights sum to its reach
+int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerged *out,
+                 const int32_t *sub_k = nullptr);
 
 // ------------------------------------------------------- graph kernels
 int launch_validate(Ctx &ctx, const DevGraph &g, int *d_flags);
@@ -271,6 +273,8 @@ struct BcInput {
   double *bcp = nullptr;          // accumulation target, indexed by vertex
 };
 
+enum { LARGE_PATH_AUTO = 0, LARGE_PATH_WIDE = 1, LARGE_PATH_BATCHED = 2, LARGE_PATH_PER_SOURCE = 3 };
+
 struct BcPlanOpts {
   bool fp32_delta = false;
   const int64_t *sources = nullptr;  // host; nullable = every vertex
@@ -280,6 +284,12 @@ struct BcPlanOpts {
   const int64_t *srcmap = nullptr;
   bool force_large = false;           // route every piece through the global path
   bool per_source_large = false;      // large pieces one source per CTA (no 32-source batches)
+  // large-piece kernel: 0 chosen by the plan (or the autotuner), else one of
+  // the LARGE_PATH_* values (the BCS_LARGE_PATH variable overrides it)
+  int large_path = 0;
+  // shared memory a piece may need for one source to take the small path
+  // (0: the default limit); set by the autotuner's threshold candidates
+  size_t small_limit = 0;
   // debug output for a single source (large path only)
   int32_t *dbg_d = nullptr;
   double *dbg_sig = nullptr;

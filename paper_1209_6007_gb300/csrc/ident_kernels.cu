@@ -179,36 +179,55 @@ __global__ void k_ident_corr(int64_t nslots, const int64_t *__restrict__ srow, c
   }
 }
 
-// unequal reach: R and Q of every class, on its representative
+// unequal reach: R, Q and K of every class, on its representative.  With
+// sub_k (the preprocessing loop's later rounds) a slot is a sub-unit of
+// sub_k[x] members of total weight reach[x]; else one member.
 __global__ void k_ident_sums(int64_t nslots, const int32_t *__restrict__ cls, const int32_t *__restrict__ reach,
-                             unsigned long long *rsum, unsigned long long *qsum) {
+                             const int32_t *__restrict__ sub_k, unsigned long long *rsum, unsigned long long *qsum,
+                             unsigned long long *ksum) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nslots; x += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long r = (unsigned long long)reach[x];
     atomicAdd(rsum + cls[x], r);
     atomicAdd(qsum + cls[x], r * r);
+    atomicAdd(ksum + cls[x], (unsigned long long)(sub_k ? sub_k[x] : 1));
   }
 }
 
 // unequal reach: the neighbour terms (on representatives, as corr) and each
-// copy's own terms (slot_corr); N[p] = size of piece p's connected component
+// copy's own terms (slot_corr); N[p] = size of piece p's connected component.
+// A slot x of weight T_x standing for k_x members of weight t_x = T_x / k_x
+// each, in a class of K members and weight T:
+//   each member of x:            (t_x - T/K)(N_C - T) + (t_x - 1)(T - T_x)
+//   type I, each member of a neighbour:  (T^2 - sum T_x^2) / K_N,
+//                                K_N = the members of the class's neighbours
+// (pairs inside a sub-unit were counted when it formed; with one member per
+// slot these are the terms above).
 __global__ void k_ident_corr_unequal(int64_t nslots, const int64_t *__restrict__ srow,
                                      const int32_t *__restrict__ scol, const int32_t *__restrict__ reach,
-                                     const int32_t *__restrict__ piece, const int64_t *__restrict__ N,
-                                     const int32_t *__restrict__ cls, const int32_t *__restrict__ cnt,
-                                     const int8_t *__restrict__ typ, const unsigned long long *__restrict__ rsum,
-                                     const unsigned long long *__restrict__ qsum, double *corr, double *slot_corr) {
+                                     const int32_t *__restrict__ sub_k, const int32_t *__restrict__ piece,
+                                     const int64_t *__restrict__ N, const int32_t *__restrict__ cls,
+                                     const int32_t *__restrict__ cnt, const int8_t *__restrict__ typ,
+                                     const unsigned long long *__restrict__ rsum,
+                                     const unsigned long long *__restrict__ qsum,
+                                     const unsigned long long *__restrict__ ksum, double *corr, double *slot_corr) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nslots; x += (int64_t)gridDim.x * blockDim.x) {
     const int32_t c = cls[x];
-    const int64_t K = cnt[c];
-    if (K < 2) {
+    if (cnt[c] < 2) {
       slot_corr[x] = 0.0;
       continue;
     }
-    const int64_t R = (int64_t)rsum[c], r = reach[x], NC = N[piece[x]];
-    slot_corr[x] = (double)((r - 1) * (R - r)) + ((double)r - (double)R / (double)K) * (double)(NC - R);
+    const int64_t R = (int64_t)rsum[c], NC = N[piece[x]];
+    const double K = (double)ksum[c], T = (double)R, Tx = (double)reach[x];
+    const double tx = Tx / (double)(sub_k ? sub_k[x] : 1);
+    slot_corr[x] = (tx - T / K) * (double)(NC - R) + (tx - 1.0) * (T - Tx);
     if (c == x && typ[c] == 1) {
       const int64_t b = srow[c], e = srow[c + 1];
-      const double amt = (double)(R * R - (int64_t)qsum[c]) / (double)(e - b);
+      int64_t KN = e - b;
+      if (sub_k) {
+        KN = 0;
+        for (int64_t k = b; k < e; k++) KN += sub_k[scol[k]];
+      }
+      const double amt = (double)(R * R - (int64_t)qsum[c]) / (double)KN;
       for (int64_t k = b; k < e; k++) {
         const int32_t y = scol[k];
         if (cls[y] == y) atomicAdd(corr + y, amt);
@@ -239,8 +258,9 @@ __global__ void k_merge_emit(int64_t nslots, const int64_t *__restrict__ srow, c
                              const int64_t *__restrict__ mrow_scan, const int32_t *__restrict__ org,
                              const int32_t *__restrict__ reach, const int32_t *__restrict__ cnt,
                              const double *__restrict__ corr, const unsigned long long *__restrict__ rsum,
-                             int64_t *mrow, int32_t *mcol, int32_t *morg, int32_t *mreach, int32_t *mident,
-                             double *mcorr, double *minit, int32_t *slot_to_m) {
+                             const unsigned long long *__restrict__ ksum, int64_t *mrow, int32_t *mcol,
+                             int32_t *morg, int32_t *mreach, int32_t *mident, double *mcorr, double *minit,
+                             int32_t *slot_to_m) {
   for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nslots; x += (int64_t)gridDim.x * blockDim.x) {
     slot_to_m[x] = (int32_t)mslot[cls[x]];
     if (cls[x] != x) continue;
@@ -254,9 +274,10 @@ __global__ void k_merge_emit(int64_t nslots, const int64_t *__restrict__ srow, c
     }
     morg[m] = org[x];
     mreach[m] = reach[x];
-    mident[m] = cnt ? cnt[x] : 1;
+    const int64_t K = ksum ? (int64_t)ksum[x] : (cnt ? cnt[x] : 1);  // members
+    mident[m] = (int32_t)K;
     mcorr[m] = corr ? corr[x] : 0.0;
-    if (minit) minit[m] = (double)rsum[x] / (double)(cnt ? cnt[x] : 1) - 1.0;
+    if (minit) minit[m] = (double)rsum[x] / (double)K - 1.0;
   }
 }
 
@@ -275,7 +296,7 @@ __global__ void k_iota32(int64_t n, int32_t *p) {
     p[i] = (int32_t)i;
 }
 
-int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerged *out) {
+int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerged *out, const int32_t *sub_k) {
   unequal = unequal && identical;
   const int64_t P = pc.npieces, S = pc.nslots;
   out->npieces = P;
@@ -291,7 +312,7 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerge
   DBuf<int32_t> cls, cnt;
   DBuf<int8_t> typ;
   DBuf<double> corr;
-  DBuf<unsigned long long> rsum, qsum;
+  DBuf<unsigned long long> rsum, qsum, ksum;
   BCS_TRY(cls.alloc(S, ctx.stream));
   if (identical && S > 0) {
     DBuf<uint64_t> fo, fc;
@@ -321,12 +342,15 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerge
     if (unequal) {
       BCS_TRY(rsum.alloc(S, ctx.stream));
       BCS_TRY(qsum.alloc(S, ctx.stream));
+      BCS_TRY(ksum.alloc(S, ctx.stream));
       BCS_TRY(out->slot_corr.alloc(S, ctx.stream));
       BCS_CUDA(cudaMemsetAsync(rsum.p, 0, S * sizeof(unsigned long long), ctx.stream));
       BCS_CUDA(cudaMemsetAsync(qsum.p, 0, S * sizeof(unsigned long long), ctx.stream));
-      k_ident_sums<<<gs, block, 0, ctx.stream>>>(S, cls.p, sreach, rsum.p, qsum.p);
-      k_ident_corr_unequal<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, spiece, out->piece_N.p, cls.p, cnt.p,
-                                                         typ.p, rsum.p, qsum.p, corr.p, out->slot_corr.p);
+      BCS_CUDA(cudaMemsetAsync(ksum.p, 0, S * sizeof(unsigned long long), ctx.stream));
+      k_ident_sums<<<gs, block, 0, ctx.stream>>>(S, cls.p, sreach, sub_k, rsum.p, qsum.p, ksum.p);
+      k_ident_corr_unequal<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, sub_k, spiece, out->piece_N.p, cls.p,
+                                                         cnt.p, typ.p, rsum.p, qsum.p, ksum.p, corr.p,
+                                                         out->slot_corr.p);
       ctx.launches += 2;
     } else {
       k_ident_corr<<<gs, block, 0, ctx.stream>>>(S, srow, scol, sreach, cls.p, cnt.p, typ.p, corr.p);
@@ -371,7 +395,8 @@ int device_merge(Ctx &ctx, DevPieces &pc, bool identical, bool unequal, DevMerge
   if (S > 0) {
     k_merge_emit<<<gs, block, 0, ctx.stream>>>(S, srow, scol, cls.p, spiece, piece_off, mslot.p, mrow_scan.p,
                                                out->slot_org.p, sreach, identical ? cnt.p : nullptr,
-                                               identical ? corr.p : nullptr, unequal ? rsum.p : nullptr, out->mrow.p,
+                                               identical ? corr.p : nullptr, unequal ? rsum.p : nullptr,
+                                               unequal ? ksum.p : nullptr, out->mrow.p,
                                                out->mcol.p, out->morg.p, out->mreach.p, out->mident.p, out->mcorr.p,
                                                unequal ? out->minit.p : nullptr, out->slot_to_m.p);
     ctx.launches++;

@@ -1,23 +1,34 @@
-// resplit.cu - one more articulation split after identical-vertex merging
-// (the preprocessing of Section 3.4 repeated once: merging can leave a
-// merged vertex as a cut vertex, Fig. 3).
+// resplit.cu - the preprocessing of Section 3.4 repeated to a fixpoint:
+// merging identical vertices can leave a merged vertex as a cut vertex
+// (Fig. 3), and splitting there can make copies identical to other
+// vertices of their block, so split and merge alternate until a round
+// merges nothing.
 //
-// The merged pieces are taken as a graph of their own (merged vertices,
-// global ids) whose vertex v weighs T[v] = reach[v] * ident[v] (a merged
-// vertex stands for ident[v] members of reach[v] each; with classes of
-// unequal reach, T is the class's reach sum), and split into biconnected
-// blocks by the same device code as the input graph.  A copy of v in a
-// block then weighs T[v] plus everything beyond v away from that block, as
-// for any cut vertex (Eq. 4 with weights).  When v stands for k identical
-// members, every path across v goes through exactly one of them, so in the
-// block each member carries 1/k of the weight beyond it: the copy keeps
-// ident k and its dependency starts at T_copy / k - 1, a fractional start
-// the Bc-Reach kernels already take (so does its source weight, T_copy).
-// A merged leaf is the two-vertex block case of the same rule.  The blocks'
-// bc' are added to the merged vertices, whose own map-back then runs as
-// before.
+// A round takes the current pieces as a graph of their own (their
+// vertices, global ids) whose vertex v weighs T[v] = reach[v] * ident[v] (a
+// merged vertex stands for ident[v] members of reach[v] each; with classes
+// of unequal reach, T is the class's reach sum), and splits it into
+// biconnected blocks by the same device code as the input graph.  A copy of
+// v in a block then weighs T[v] plus everything beyond v away from that
+// block, as for any cut vertex (Eq. 4 with weights).  When v stands for k
+// identical members, every path across v goes through exactly one of them,
+// so in the block each member carries 1/k of the weight beyond it.  The
+// blocks' identical vertices are then merged with classes keyed on the
+// neighbourhood alone, each copy being a sub-unit of k members of total
+// weight T_copy: the class of K members and weight T keeps ident K, its
+// dependency starts at T / K - 1 (a fractional start the Bc-Reach kernels
+// already take) and its source weight is T; the per-member and neighbour
+// terms of a class of sub-units are added in closed form (ident_kernels.cu).
+// A merged leaf is the two-vertex block case of the same rule.  Bc-Reach
+// runs on the last round's pieces; bc' then goes back one round at a time
+// (a copy's value onto the vertex it copies, with its own terms) until it
+// reaches the first merge's vertices, whose own map-back runs as before.
+// Every round's pieces are a valid Bc-Reach input, so the loop may stop
+// early (FIX_MAX_ROUNDS) without changing the result.
 #include <algorithm>
 #include <cmath>
+#include <memory>
+#include <vector>
 
 #include "common.h"
 
@@ -65,25 +76,23 @@ __global__ void k_rs_graph(int64_t M, const int64_t *__restrict__ piece_off, int
   }
 }
 
-// ident of each new piece vertex (its merged vertex's) and its dependency
-// start T_copy / ident - 1
-__global__ void k_rs_weights(int64_t M2, const int32_t *__restrict__ morg2, const int32_t *__restrict__ treach,
-                             const int32_t *__restrict__ mident, int32_t *ident2, double *init2) {
-  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < M2; x += (int64_t)gridDim.x * blockDim.x) {
-    const int32_t k = mident ? mident[morg2[x]] : 1;
-    ident2[x] = k;
-    init2[x] = (double)treach[x] / (double)k - 1.0;
-  }
+// the members each slot of a round's pieces stands for: its vertex's ident
+__global__ void k_rs_subk(int64_t S, const int32_t *__restrict__ slot_org, const int32_t *__restrict__ mident,
+                          int32_t *sub_k) {
+  for (int64_t x = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; x < S; x += (int64_t)gridDim.x * blockDim.x)
+    sub_k[x] = mident ? mident[slot_org[x]] : 1;
 }
 
 }  // namespace
 
-int run_bcreach_resplit(Ctx &ctx, DevMerged &m, const BcInput &in, const BcPlanOpts &po) {
-  const int64_t M = m.nmerged, P = m.npieces, E = m.nentries;
-  if (M == 0 || P == 0) return BCS_OK;
-  Tracer tr("resplit", ctx.stream);
+constexpr int FIX_MAX_ROUNDS = 64;
+
+// One round: split the pieces of `cur` at their cut vertices (weights T)
+// and, with `merge`, merge the identical vertices of the blocks.
+static int split_and_merge(Ctx &ctx, DevMerged &cur, bool ident, bool merge, DevMerged *next) {
+  const int64_t M = cur.nmerged, P = cur.npieces, E = cur.nentries;
   const int maxb = ctx.num_sms * 16;
-  DBuf<int32_t> gcol, T, label;
+  DBuf<int32_t> gcol, T, label, sub_k;
   DBuf<int64_t> N;
   DBuf<uint8_t> alive;
   BCS_TRY(gcol.alloc(std::max<int64_t>(E, 1), ctx.stream));
@@ -91,59 +100,87 @@ int run_bcreach_resplit(Ctx &ctx, DevMerged &m, const BcInput &in, const BcPlanO
   BCS_TRY(label.alloc(M, ctx.stream));
   BCS_TRY(N.alloc(M, ctx.stream));
   BCS_TRY(alive.alloc(M, ctx.stream));
-  k_rs_graph<<<rs_grid(M, maxb), RS_BLOCK, 0, ctx.stream>>>(M, m.piece_off.p, P, m.piece_N.p, m.mrow.p, m.mcol.p,
-                                                           m.mreach.p, in.ident ? m.mident.p : nullptr, m.minit.p,
-                                                           gcol.p, T.p, N.p, label.p, alive.p);
+  k_rs_graph<<<rs_grid(M, maxb), RS_BLOCK, 0, ctx.stream>>>(M, cur.piece_off.p, P, cur.piece_N.p, cur.mrow.p,
+                                                           cur.mcol.p, cur.mreach.p, ident ? cur.mident.p : nullptr,
+                                                           cur.minit.p, gcol.p, T.p, N.p, label.p, alive.p);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
   DevGraph g2;
   g2.n = M;
   g2.nnz = E;
-  g2.rp = m.mrow.p;
+  g2.rp = cur.mrow.p;
   g2.col = gcol.p;
   DevPieces pc2;
   BCS_TRY(device_pieces(ctx, g2, alive.p, T.p, N.p, label.p, true, &pc2));
-  tr.mark("blocks");
-  DevMerged m2;
-  BCS_TRY(device_merge(ctx, pc2, false, false, &m2));
-  tr.mark("compact");
-  const int64_t M2 = m2.nmerged, P2 = m2.npieces;
-  ctx.stats.n_pieces = P2;
-  if (M2 == 0 || P2 == 0) return BCS_OK;
-  DBuf<int32_t> ident2;
-  DBuf<double> init2;
-  BCS_TRY(ident2.alloc(M2, ctx.stream));
-  BCS_TRY(init2.alloc(M2, ctx.stream));
-  k_rs_weights<<<rs_grid(M2, maxb), RS_BLOCK, 0, ctx.stream>>>(M2, m2.morg.p, m2.mreach.p,
-                                                               in.ident ? m.mident.p : nullptr, ident2.p, init2.p);
-  ctx.launches++;
-  BCS_CUDA(cudaGetLastError());
-  // a new piece lies inside one merged piece: the sum of ident over a
-  // vertex's neighbours is bounded as it was there
-  int32_t fan = 1;
-  for (int32_t d : m.h_piece_maxdeg) fan = std::max(fan, d);
-  std::vector<CompDesc> comps2(P2);
-  for (int64_t p = 0; p < P2; p++) {
-    CompDesc c;
-    c.vtx_off = m2.h_piece_off[p];
-    c.row_off = m2.h_piece_off[p];
-    c.n = (int32_t)(m2.h_piece_off[p + 1] - m2.h_piece_off[p]);
-    c.maxdeg = std::max<int32_t>(1, m2.h_piece_maxdeg[p]);
-    c.nnz = m2.h_piece_ent[p];
-    c.fan = (double)fan;
-    comps2[p] = c;
+  if (!merge) return device_merge(ctx, pc2, false, false, next);  // every copy keeps reach T_copy
+  // classes keyed on the neighbourhood alone; a class of one slot keeps its
+  // copy's ident k and dependency start T_copy / k - 1
+  const int64_t S2 = pc2.nslots;
+  BCS_TRY(sub_k.alloc(std::max<int64_t>(S2, 1), ctx.stream));
+  if (S2 > 0) {
+    k_rs_subk<<<rs_grid(S2, maxb), RS_BLOCK, 0, ctx.stream>>>(S2, pc2.slot_org.p, ident ? cur.mident.p : nullptr,
+                                                             sub_k.p);
+    ctx.launches++;
+    BCS_CUDA(cudaGetLastError());
   }
-  BcInput b;
-  b.row = m2.mrow.p;
-  b.col = m2.mcol.p;
-  b.reach = m2.mreach.p;
-  b.ident = in.ident ? ident2.p : nullptr;
-  b.init = init2.p;
-  b.bcp = m2.mcorr.p;  // zero: nothing merged in this pass
-  BCS_TRY(run_bcreach(ctx, comps2, b, po));
-  tr.mark("bcreach");
-  // each new piece vertex's bc' onto its merged vertex
-  BCS_TRY(launch_mapback(ctx, m2.nslots, m2.slot_org.p, m2.slot_to_m.p, m2.mcorr.p, in.bcp));
+  return device_merge(ctx, pc2, true, true, next, sub_k.p);
+}
+
+int run_bcreach_resplit(Ctx &ctx, DevMerged &m, const BcInput &in, const BcPlanOpts &po) {
+  if (m.nmerged == 0 || m.npieces == 0) return BCS_OK;
+  Tracer tr("resplit", ctx.stream);
+  const bool ident = in.ident != nullptr;
+  // rounds[r]: the pieces after round r + 1 (its slots are copies of the
+  // vertices of the round before, or of m)
+  std::vector<std::unique_ptr<DevMerged>> rounds;
+  DevMerged *cur = &m;
+  for (int r = 0; r < FIX_MAX_ROUNDS; r++) {
+    rounds.emplace_back(new DevMerged());
+    DevMerged *next = rounds.back().get();
+    BCS_TRY(split_and_merge(ctx, *cur, ident, ident, next));
+    tr.mark("round");
+    cur = next;
+    // nothing merged: splitting again would give the same blocks
+    if (!ident || next->nmerged == next->nslots || next->nmerged == 0) break;
+  }
+  ctx.stats.n_rounds = (int64_t)rounds.size();
+  DevMerged &last = *cur;
+  const int64_t P2 = last.npieces;
+  ctx.stats.n_pieces = P2;
+  if (last.nmerged > 0 && P2 > 0) {
+    // a piece lies inside one piece of the first merge: the sum of ident over
+    // a vertex's neighbours is bounded by the original degrees, as it was there
+    int32_t fan = 1;
+    for (int32_t d : m.h_piece_maxdeg) fan = std::max(fan, d);
+    std::vector<CompDesc> comps2(P2);
+    for (int64_t p = 0; p < P2; p++) {
+      CompDesc c;
+      c.vtx_off = last.h_piece_off[p];
+      c.row_off = last.h_piece_off[p];
+      c.n = (int32_t)(last.h_piece_off[p + 1] - last.h_piece_off[p]);
+      c.maxdeg = std::max<int32_t>(1, last.h_piece_maxdeg[p]);
+      c.nnz = last.h_piece_ent[p];
+      c.fan = (double)fan;
+      comps2[p] = c;
+    }
+    BcInput b;
+    b.row = last.mrow.p;
+    b.col = last.mcol.p;
+    b.reach = last.mreach.p;
+    b.ident = ident ? last.mident.p : nullptr;
+    b.init = last.minit.p;
+    b.bcp = last.mcorr.p;  // starts with the last round's neighbour terms
+    BCS_TRY(run_bcreach(ctx, comps2, b, po));
+    tr.mark("bcreach");
+  }
+  // bc' back one round at a time: each copy's value (and its own terms) onto
+  // the vertex it copies
+  for (int64_t r = (int64_t)rounds.size() - 1; r >= 0; r--) {
+    DevMerged &x = *rounds[r];
+    double *prev = r > 0 ? rounds[r - 1]->mcorr.p : in.bcp;
+    if (x.nslots > 0)
+      BCS_TRY(launch_mapback(ctx, x.nslots, x.slot_org.p, x.slot_to_m.p, x.mcorr.p, prev, x.slot_corr.p));
+  }
   return BCS_OK;
 }
 

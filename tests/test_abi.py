@@ -85,11 +85,11 @@ def test_host_side_argument_checks():
 
 def test_step_bits_checked_on_the_host():
     """BCS_STEP_S, BCS_STEP_U and BCS_STEP_L are taken by the shattered calls
-    (at most one of them), BCS_STEP_O by all but the batch call, and unknown
-    bits are rejected before any device work."""
+    (S with neither U nor L; U and L together), BCS_STEP_O by all but the
+    batch call, and unknown bits are rejected before any device work."""
     import paper_1209_6007_gb300 as bcs
     rp, col = np.array([0, 1, 2], np.int64), np.array([1, 0], np.int32)
-    pairs = (bcs.STEP_S | bcs.STEP_U, bcs.STEP_S | bcs.STEP_L, bcs.STEP_U | bcs.STEP_L)
+    pairs = (bcs.STEP_S | bcs.STEP_U, bcs.STEP_S | bcs.STEP_L, bcs.STEP_S | bcs.STEP_U | bcs.STEP_L)
     for steps in (128, 256 | bcs.STEP_S) + tuple(bcs.STEPS_ALL | p for p in pairs):
         with pytest.raises(bcs.BcsError) as e:
             bcs.bc_shattered(rp, col, steps=steps)
@@ -106,6 +106,8 @@ def test_step_bits_checked_on_the_host():
                  lambda: bcs.bc_shattered(rp, col, side=True, order=True),
                  lambda: bcs.bc_shattered(rp, col, unequal=True, order=True),
                  lambda: bcs.bc_shattered(rp, col, resplit=True, order=True),
+                 lambda: bcs.bc_shattered(rp, col, resplit=True, unequal=True),
+                 lambda: bcs.bc_shattered_batch([0, 2], rp, col, resplit=True, unequal=True),
                  lambda: bcs.bc_shattered_batch([0, 2], rp, col, resplit=True),
                  lambda: bcs.bc_shattered_batch([0, 2], rp, col, side=True),
                  lambda: bcs.bc_shattered_batch([0, 2], rp, col, unequal=True)):

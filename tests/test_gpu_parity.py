@@ -130,6 +130,41 @@ def test_autotuned_split_gives_the_same_result(gpu):
         assert st["small_smem_budget"] in (100 * 1024, 72 * 1024, 54 * 1024)
 
 
+def test_autotuned_threshold_gives_the_same_result(gpu):
+    """Pieces of about a thousand vertices need between 40 and 100 KB of
+    shared memory for one source, between the threshold candidates: the
+    autotuner times the candidates over the pieces (into a scratch
+    accumulator), keeps one, and the result, with FP64 and FP32 dependencies,
+    is the oracle's; later calls reuse the choice."""
+    g = gg.disjoint_union(*[gg.chung_lu(n, 2.5, 8.0, n) for n in (700, 1000, 1300, 1600)],
+                          gg.config(2, scale_pct=1))
+    ref = oracle.bc(g)
+    limits = set()
+    for fp32, tol in ((False, TOL64), (True, TOL32), (False, TOL64)):
+        assert rel(gpu.bc_shattered(g.row_ptr, g.col, autotune=True, delta_fp32=fp32), ref) <= tol
+        st = gpu.last_stats()
+        assert st["tuned"] & 1
+        assert st["small_limit"] in (100 * 1024, 64 * 1024, 40 * 1024)
+        limits.add(st["small_limit"])
+    assert len(limits) == 1
+    gpu.bc_shattered(g.row_ptr, g.col)
+    assert gpu.last_stats()["small_limit"] == 100 * 1024  # without the autotuner: the fixed limit
+
+
+def test_autotuned_large_kernel_gives_the_same_result(gpu):
+    """A piece with thousands of sources: the autotuner times the whole-GPU
+    kernel, 32-source batches and one source per CTA on samples of its
+    sources, runs the piece on the fastest, and the result is the oracle's."""
+    g = gg.chung_lu(8000, 2.3, 6.0, 21)
+    ref = oracle.bc(g)
+    for fp32, tol in ((False, TOL64), (True, TOL32)):
+        assert rel(gpu.bc_shattered(g.row_ptr, g.col, autotune=True, delta_fp32=fp32), ref) <= tol
+        st = gpu.last_stats()
+        assert st["tuned"] in (1 << 1, 1 << 2, 1 << 3)
+        assert st["n_large_sources"] > 0
+    assert rel(gpu.bc_plain(g.row_ptr, g.col, autotune=True), ref) <= TOL64
+
+
 def test_shattered_articulation_scaled(gpu):
     """Config 2 at 5% of its blocks: full oracle in seconds, many pieces."""
     g = gg.config(2, scale_pct=5)
@@ -504,6 +539,66 @@ def test_resplit_on_a_large_piece(gpu, path, monkeypatch):
     ref = oracle.bc(g)
     assert rel(gpu.bc_shattered(g.row_ptr, g.col, resplit=True), ref) <= TOL64
     assert gpu.last_stats()["n_large_sources"] > 0
+
+
+# ------------------------- the preprocessing loop repeated to a fixpoint
+def blown_up(seed):
+    """The blown-up graphs of the CPU fixpoint check (tests/test_readings.py)."""
+    rng = np.random.default_rng(100 + seed)
+    nb = int(rng.integers(3, 8))
+    base = gg.random_tree(nb, seed) if seed % 2 else gg.gnp(nb, 0.5, seed)
+    return gg.blow_up(base, seed, max_k=3, p_closed=0.3, n_pend=int(rng.integers(0, 4)))
+
+
+@pytest.mark.parametrize("unequal", [False, True])
+def test_fixpoint_loop_on_blown_up_graphs(gpu, unequal):
+    """Split and merge repeated until a round merges nothing: bc equal to the
+    oracle's, over graphs needing up to four rounds, with every step subset
+    that merges (one round without identical merging)."""
+    rounds = []
+    for seed in range(24):
+        g = blown_up(seed)
+        ref = oracle.bc(g)
+        for steps in (ALL, oracle.STEP_A | oracle.STEP_I, oracle.STEP_I, oracle.STEP_D | oracle.STEP_A):
+            got = gpu.bc_shattered(g.row_ptr, g.col, steps=steps, resplit=True, unequal=unequal)
+            assert rel(got, ref) <= TOL64, (seed, steps)
+            r = gpu.last_stats()["n_rounds"]
+            if steps & oracle.STEP_I:
+                rounds.append(r)
+            else:
+                assert r <= 1  # one split, none when nothing is left after peeling
+        got = gpu.bc_shattered(g.row_ptr, g.col, resplit=True, unequal=unequal, delta_fp32=True)
+        assert rel(got, ref) <= TOL32
+    assert max(rounds) >= 3
+
+
+def test_fixpoint_loop_on_a_nested_four_cycle(gpu):
+    """C4 blown up: the first merge takes each pair of opposite corner groups
+    into one vertex, leaving one edge; round 1 splits it off and merges its
+    closed pair, round 2 finds nothing left to merge."""
+    g = gg.blow_up(gg.cycle(4), 3, max_k=3, p_closed=0.0)
+    assert rel(gpu.bc_shattered(g.row_ptr, g.col, resplit=True), oracle.bc(g)) <= TOL64
+    assert gpu.last_stats()["n_rounds"] == 2
+
+
+@pytest.mark.parametrize("path", LARGE_PATHS)
+def test_fixpoint_loop_larger_graphs_and_batch(gpu, path, monkeypatch):
+    """A blown-up random tree with extra edges (thousands of vertices, pieces
+    on the large-piece path too) and a batch of blown-up graphs."""
+    monkeypatch.setenv("BCS_LARGE_PATH", path)
+    base = gg.disjoint_union(gg.random_tree(300, 4), gg.gnp(40, 0.15, 2))
+    g = gg.blow_up(base, 9, max_k=4, p_closed=0.3, n_pend=200)
+    ref = oracle.bc(g)
+    for unequal in (False, True):
+        assert rel(gpu.bc_shattered(g.row_ptr, g.col, resplit=True, unequal=unequal), ref) <= TOL64
+        assert gpu.last_stats()["n_rounds"] >= 2
+    rp, col = on_device(g)
+    got = gpu.bc_shattered(rp, col, resplit=True, unequal=True, delta_fp32=True).cpu().numpy()
+    assert rel(got, ref) <= TOL32
+    graphs = [blown_up(s) for s in range(10)]
+    h = gg.disjoint_union(*graphs)
+    off = np.cumsum([0] + [x.n for x in graphs])
+    assert rel(gpu.bc_shattered_batch(off, h.row_ptr, h.col, resplit=True, unequal=True), oracle.bc(h)) <= TOL64
 
 
 # --------------------------------------------------------------- errors
