@@ -55,7 +55,12 @@ namespace bcs {
 constexpr int WIDE_THREADS = 256;
 constexpr int WIDE_WARPS = WIDE_THREADS / 32;
 constexpr int WIDE_CH = 128;  // row entries per item of a long row
-constexpr int WIDE_GRAB = 2;  // bitmap words (or long-row items) a warp takes at a time
+// The light rows of a pass are handed out in units of WIDE_UNIT vertices (a
+// part of a bitmap word), WIDE_GRAB units (or long-row items) at a time:
+// small enough that the last warps of a pass finish soon after the others.
+constexpr int WIDE_UNIT = 8;
+constexpr int WIDE_UPW = 32 / WIDE_UNIT;  // units per bitmap word
+constexpr int WIDE_GRAB = 2;
 // The work of a pass is handed out from WIDE_SHARDS counters on separate
 // cache lines (one address would serialise every warp's grab).
 constexpr int WIDE_SHARDS = 8;
@@ -161,6 +166,13 @@ __device__ __forceinline__ int64_t wide_grab(int32_t *ctrs, int64_t total, int &
     const unsigned rot = (bm | (bm << WIDE_SHARDS)) >> (shard + 1);
     shard = (shard + __ffs(rot)) % WIDE_SHARDS;
   }
+}
+
+// the light vertices of unit ku of a level's bitmap, as the bits of its word
+__device__ __forceinline__ uint32_t unit_bits(const uint32_t *bits, const uint32_t *heavy, int64_t ku, int64_t &wd) {
+  wd = ku / WIDE_UPW;
+  const uint32_t sel = (WIDE_UNIT == 32 ? 0xffffffffu : ((1u << WIDE_UNIT) - 1u)) << ((ku % WIDE_UPW) * WIDE_UNIT);
+  return __ldcg(bits + wd) & ~__ldg(heavy + wd) & sel;
 }
 
 template <int SPL>
@@ -343,12 +355,12 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       // bitmap's words (light rows), handed out WIDE_GRAB at a time
       int shard = (int)((gtid >> 5) % WIDE_SHARDS);
       for (;;) {
-        const int64_t w0 = wide_grab(S.wctr + (size_t)2 * L * WIDE_SHARDS * 32, S.nwords + nh, shard, lane);
+        const int64_t w0 = wide_grab(S.wctr + (size_t)2 * L * WIDE_SHARDS * 32, S.nwords * WIDE_UPW + nh, shard, lane);
         if (w0 < 0) break;
-        for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords + nh); wi++) {
+        for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords * WIDE_UPW + nh); wi++) {
           if (wi >= nh) {
-            const int64_t wd = wi - nh;
-            uint32_t m = __ldcg(bits_cur + wd) & ~__ldg(S.heavy + wd);
+            int64_t wd;
+            uint32_t m = unit_bits(bits_cur, S.heavy, wi - nh, wd);
             while (m) {
               const int32_t v = (int32_t)(wd * 32 + __ffs(m) - 1);
               m &= m - 1u;
@@ -453,12 +465,12 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       };
       int shard = (int)((gtid >> 5) % WIDE_SHARDS);
       for (;;) {
-        const int64_t w0 = wide_grab(S.wctr + (size_t)(2 * l + 1) * WIDE_SHARDS * 32, S.nwords + nh, shard, lane);
+        const int64_t w0 = wide_grab(S.wctr + (size_t)(2 * l + 1) * WIDE_SHARDS * 32, S.nwords * WIDE_UPW + nh, shard, lane);
         if (w0 < 0) break;
-        for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords + nh); wi++) {
+        for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords * WIDE_UPW + nh); wi++) {
           if (wi >= nh) {
-            const int64_t wd = wi - nh;
-            uint32_t m = __ldcg(bits_l + wd) & ~__ldg(S.heavy + wd);
+            int64_t wd;
+            uint32_t m = unit_bits(bits_l, S.heavy, wi - nh, wd);
             while (m) {
               const int32_t v = (int32_t)(wd * 32 + __ffs(m) - 1);
               m &= m - 1u;
