@@ -248,9 +248,12 @@ def roofline(st: dict, clk: dict, peaks: dict, n_sm: int) -> dict:
     call counted over its (source, entry) pairs.  Per launch: the sum over
     processed sources of these bytes, over the kernel's CUDA-event time.
 
-    Shared-memory pieces only: the FP64 pipe, as 2 FLOP per DAG edge plus 9
-    per (source, vertex), against 152 SMs x 4 FP64 FLOP/clk at the sampled
-    clock."""
+    Shared-memory pieces only: the issue rate, the kernel's warp
+    instructions per launch (ncu, committed summary of the same command)
+    over its CUDA-event time against 152 SMs x 4 schedulers x 1 warp
+    instruction per clock at the sampled clock, with the lanes active per
+    instruction beside it; the FP64 figure (2 FLOP per DAG edge plus 9 per
+    (source, vertex) against 4 FP64 FLOP/clk per SM) is reported too."""
     dag = float(st["dag_edges"])
     wse, wsv = float(st["work_sources_entries"]), float(st["work_sources_vertices"])
     sm_mhz = clk.get("sm_mhz") or float(peaks.get("sm_max_mhz", 2070.0))
@@ -273,14 +276,25 @@ def roofline(st: dict, clk: dict, peaks: dict, n_sm: int) -> dict:
     flop = 2.0 * dag + 9.0 * wsv
     ms = st["ms_bcreach_small"]
     fp64_peak = n_sm * 4.0 * sm_mhz * 1e6 / 1e12
-    achieved = flop / (ms / 1e3) / 1e12 if ms > 0 else None
+    fp64 = flop / (ms / 1e3) / 1e12 if ms > 0 else None
     rec = measured_traffic("small")
-    return {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-            "frac": (achieved / fp64_peak) if achieved else None,
-            "traffic": rec["dram_bytes_per_launch"] if rec else None,
-            "kernel": "k_bcreach_small (FP64 dependencies)",
-            "peak_source": f"derived: {n_sm} SMs x 4 FP64 FLOP/clk x {sm_mhz:.0f} MHz (sampled)",
-            "work": {"dag_edges": dag, "source_vertices": wsv, "flop": flop, "ms": ms}}
+    fp64_rec = {"achieved": fp64, "peak": fp64_peak, "unit": "TFLOP/s", "frac": (fp64 / fp64_peak) if fp64 else None,
+                "peak_source": f"derived: {n_sm} SMs x 4 FP64 FLOP/clk x {sm_mhz:.0f} MHz (sampled)"}
+    work = {"dag_edges": dag, "source_vertices": wsv, "flop": flop, "ms": ms}
+    if rec and rec.get("warp_inst_per_launch") and ms > 0:
+        inst = float(rec["warp_inst_per_launch"])
+        peak = n_sm * 4.0 * sm_mhz * 1e6 / 1e9
+        achieved = inst / (ms / 1e3) / 1e9
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp instructions/s",
+                "frac": achieved / peak, "traffic": rec["dram_bytes_per_launch"],
+                "kernel": "k_bcreach_small (issue rate)",
+                "peak_source": f"derived: {n_sm} SMs x 4 schedulers x 1 warp instruction/clk x {sm_mhz:.0f} MHz "
+                               "(sampled); instructions per launch from ncu",
+                "lane_efficiency": float(rec["thread_inst_per_launch"]) / (32.0 * inst),
+                "fp64": fp64_rec, "work": {**work, "warp_instructions": inst}}
+    return {"bound": "alu", "achieved": fp64, "peak": fp64_peak, "unit": "TFLOP/s",
+            "frac": fp64_rec["frac"], "traffic": rec["dram_bytes_per_launch"] if rec else None,
+            "kernel": "k_bcreach_small (FP64 dependencies)", "peak_source": fp64_rec["peak_source"], "work": work}
 
 
 def run_ours(args):
@@ -407,17 +421,25 @@ def run_ours(args):
 
 
 def run_batch(args):
-    """Uneven batch (the batched workload's generator with a bounded largest
-    graph): `--batch-count` independent Chung-Lu graphs of log-uniform sizes
+    """Uneven batch (workload 5's generator): `--batch-count` independent
+    Chung-Lu graphs (gamma 2.3, mean degree 8) of log-uniform sizes
     16..`--batch-nmax`, packed in one CSR, all shattered and solved by one
-    bcs_bc_shattered_batch call per step.  Work = sum over the graphs of
-    n_i * m_i (every vertex a source in its own graph)."""
+    bcs_bc_shattered_batch call per step with FP32 dependencies (the timed
+    value); once with FP64 dependencies (its time and the FP32 error, over
+    the whole batch and per graph); and the baseline, plain FP64 Brandes
+    launched graph by graph (bcs_bc_plain on each graph's own CSR, on the
+    device) over a seeded stratified 1% of the graphs (one per stratum of the
+    graphs ordered by size), extrapolated to the whole batch stratum by
+    stratum.  Work = sum over the graphs of n_i * m_i (every vertex a source
+    in its own graph)."""
     import torch
     import graphgen as gg
     import paper_1209_6007_gb300 as bcs
     torch.cuda.set_device(0)
     bcs.load()
+    t0 = time.perf_counter()
     g, off = gg.batch(args.batch_count, n_min=16, n_max=args.batch_nmax)
+    gen_s = time.perf_counter() - t0
     rp = torch.from_numpy(g.row_ptr).cuda()
     col = torch.from_numpy(g.col).cuda()
     n_i = np.diff(off).astype(np.float64)
@@ -425,34 +447,76 @@ def run_batch(args):
     work = float((n_i * m_i).sum())
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        bcs.bc_shattered_batch(off, rp, col)
-    torch.cuda.synchronize()
-    clocks = ClockSampler(0)
-    clocks.start()
-    dev_ms, launches = 0.0, 0
-    for _ in range(args.steps):
+
+    def timed(fp32):
         flush.zero_()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        bcs.bc_shattered_batch(off, rp, col)
+        out = bcs.bc_shattered_batch(off, rp, col, delta_fp32=fp32, autotune=True)
         ev1.record(stream)
         ev1.synchronize()
-        dev_ms += ev0.elapsed_time(ev1)
+        return out, ev0.elapsed_time(ev1)
+
+    for _ in range(args.warmup):  # the first call also runs the autotuner
+        bcs.bc_shattered_batch(off, rp, col, delta_fp32=True, autotune=True)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    dev_ms, launches, b32 = 0.0, 0, None
+    for _ in range(args.steps):
+        b32, ms = timed(True)
+        dev_ms += ms
         launches += int(bcs.last_stats()["kernel_launches"])
     clk = clocks.stop()
     st = bcs.last_stats()
+    b64, ms64 = timed(False)  # its small-path split is tuned on this first FP64 call
+    b32, b64 = b32.cpu().numpy(), b64.cpu().numpy()
+    diff = np.abs(b32 - b64)
+    err_all = float(diff.max() / max(1.0, float(np.abs(b64).max())))
+    err_graph = float(max(diff[off[i]:off[i + 1]].max() / max(1.0, float(np.abs(b64[off[i]:off[i + 1]]).max()))
+                          for i in range(len(off) - 1) if off[i + 1] > off[i]))
+    # plain FP64 Brandes per graph on a stratified 1% of the graphs
+    order = np.argsort(n_i, kind="stable")
+    k = max(1, (len(off) - 1) // 100)
+    rng = np.random.default_rng(2026)
+    strata = np.array_split(order, k)
+    est_ms, sampled_ms, sampled = 0.0, 0.0, 0
+    for stratum in strata:
+        gi = int(rng.choice(stratum))
+        a, b = int(off[gi]), int(off[gi + 1])
+        rpg = torch.from_numpy((g.row_ptr[a:b + 1] - g.row_ptr[a]).astype(np.int64)).cuda()
+        colg = torch.from_numpy((g.col[g.row_ptr[a]:g.row_ptr[b]] - a).astype(np.int32)).cuda()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        bcs.bc_plain(rpg, colg)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        sampled_ms += ms
+        sampled += 1
+        est_ms += ms * len(stratum)
     T = dev_ms / 1e3
     line = {"metric": "BC GTEPS (sum over the batch's graphs of sources*m / s)", "value": work * args.steps / T / 1e9,
             "unit": "GTEPS", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dev_ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic",
+            "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"uneven batch: {args.batch_count} Chung-Lu graphs (gamma 2.3, mean degree 8), "
                                    f"n log-uniform 16..{args.batch_nmax}", "n": int(g.n), "m": int(g.m),
-                       "sum_n_m": work, "l2": "flushed between timed steps (256 MB write)"},
+                       "sum_n_m": work, "delta": "fp32", "l2": "flushed between timed steps (256 MB write)",
+                       "generation_s": gen_s},
             "gpu_launches": launches, "clocks": clk,
-            "stages_ms": {k: v for k, v in st.items() if k.startswith("ms_")},
-            "pieces": st["n_pieces"], "large_sources": st["n_large_sources"],
+            "stages_ms": {k2: v for k2, v in st.items() if k2.startswith("ms_")},
+            "pieces": st["n_pieces"], "large_sources": st["n_large_sources"], "tuned": st["tuned"],
+            "small_limit": st["small_limit"],
+            "fp64": {"gteps": work / (ms64 / 1e3) / 1e9, "ms": ms64, "note": "one call, small-path split tuned in it"},
+            "rel_err_fp32_vs_fp64": {"batch": err_all, "worst_graph": err_graph},
+            "per_graph_fp64_baseline": {"graphs_sampled": sampled, "strata": k, "ms_sampled": sampled_ms,
+                                        "ms_extrapolated": est_ms,
+                                        "speedup_batched_fp32": est_ms / (dev_ms / args.steps),
+                                        "method": "bcs_bc_plain per graph on the device, seeded stratified sample "
+                                                  "(one graph per stratum of the graphs ordered by size), each "
+                                                  "stratum's time = its sample's time x its graphs"},
             "note": "secondary measurement; the headline line is --workload twins"}
     print(json.dumps(line))
 

@@ -135,15 +135,17 @@ def bc_shattered(row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool 
 
 
 def bc_shattered_batch(vtx_off, row_ptr, col=None, *, steps: int = STEPS_ALL, delta_fp32: bool = False,
-                       stream=None, side: bool = False, unequal: bool = False, resplit: bool = False):
+                       stream=None, side: bool = False, unequal: bool = False, resplit: bool = False,
+                       autotune: bool = False):
     """BC of many independent graphs packed in one CSR (graph g owns the
     vertices [vtx_off[g], vtx_off[g+1]); no edge may join two graphs).
     side=True also takes side vertices out of the pieces (Section 3.3.2);
     unequal=True merges identical vertices whatever their reach; resplit=True
-    repeats splitting and merging until a round merges nothing."""
+    repeats splitting and merging until a round merges nothing; autotune as
+    for bc_shattered."""
     rp, cl = _csr_of(row_ptr, col)
     extra = (STEP_S if side else 0) | (STEP_U if unequal else 0) | (STEP_L if resplit else 0)
-    a = _Args(rp, cl, steps=steps | extra, delta_fp32=delta_fp32, stream=stream)
+    a = _Args(rp, cl, steps=steps | extra, delta_fp32=delta_fp32, stream=stream, autotune=autotune)
     off = np.ascontiguousarray(np.asarray(vtx_off, dtype=np.int64).reshape(-1))
     out, ptr = a.out(a.n)
     _check(load().bcs_bc_shattered_batch(off.ctypes.data, off.size - 1, ctypes.byref(a.csr), ctypes.byref(a.opts),

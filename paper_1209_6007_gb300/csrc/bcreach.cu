@@ -829,7 +829,7 @@ static int tune_large_piece(Ctx &ctx, const CompDesc &c, const BcInput &in, cons
   };
   const int64_t ns = nsrc_of(c), sms = ctx.num_sms;
   std::vector<Cand> cands;
-  if (wide_ok) cands.push_back({LARGE_PATH_WIDE, 128});
+  if (wide_ok) cands.push_back({LARGE_PATH_WIDE, 512});
   if (depth <= 4 * MS_DEPTH_LIMIT) cands.push_back({LARGE_PATH_BATCHED, 32 * sms});
   cands.push_back({LARGE_PATH_PER_SOURCE, 6 * sms});
   *choice = cands[0].path;

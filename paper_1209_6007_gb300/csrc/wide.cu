@@ -54,10 +54,11 @@ namespace bcs {
 
 constexpr int WIDE_THREADS = 256;
 constexpr int WIDE_WARPS = WIDE_THREADS / 32;
-constexpr int WIDE_CH = 128;  // row entries per item of a long row
+constexpr int WIDE_CH = 64;  // row entries per item of a long row
 // The light rows of a pass are handed out in units of WIDE_UNIT vertices (a
-// part of a bitmap word), WIDE_GRAB units (or long-row items) at a time:
-// small enough that the last warps of a pass finish soon after the others.
+// part of a bitmap word) when the level holds many vertices, so that the
+// last warps of the pass finish soon after the others, else whole words
+// (fewer grabs of empty units); WIDE_GRAB units (or long-row items) at a time.
 constexpr int WIDE_UNIT = 8;
 constexpr int WIDE_UPW = 32 / WIDE_UNIT;  // units per bitmap word
 constexpr int WIDE_GRAB = 2;
@@ -72,6 +73,8 @@ struct WideScratch {
   uint32_t *bits;            // [lcap][nwords]
   int32_t *flag;             // [lcap + 1] some vertex on the level
   int32_t *wctr;             // [2 lcap][WIDE_SHARDS][32] work handed out in each pass (phase 1, phase 2)
+  int32_t *lcount;           // [lcap + 1][WIDE_SHARDS][32] first reaches per level, summed over the
+                             // tiles that made them (a vertex counts once per such tile): its size, roughly
   unsigned long long *lmax;  // [lcap][32] largest stored count of (level, source), as bits
   int32_t *kshift;           // [lcap][32] power of two taken off the level's counts when pushed
   int32_t *lkind;            // [lcap + 1] 1: the level's counts are int64
@@ -168,11 +171,23 @@ __device__ __forceinline__ int64_t wide_grab(int32_t *ctrs, int64_t total, int &
   }
 }
 
-// the light vertices of unit ku of a level's bitmap, as the bits of its word
-__device__ __forceinline__ uint32_t unit_bits(const uint32_t *bits, const uint32_t *heavy, int64_t ku, int64_t &wd) {
-  wd = ku / WIDE_UPW;
-  const uint32_t sel = (WIDE_UNIT == 32 ? 0xffffffffu : ((1u << WIDE_UNIT) - 1u)) << ((ku % WIDE_UPW) * WIDE_UNIT);
+// the light vertices of unit ku of a level's bitmap (upw units per word),
+// as the bits of its word
+__device__ __forceinline__ uint32_t unit_bits(const uint32_t *bits, const uint32_t *heavy, int64_t ku, int upw,
+                                              int64_t &wd) {
+  wd = ku / upw;
+  const int ub = 32 / upw;
+  const uint32_t sel = ub == 32 ? 0xffffffffu : (((1u << ub) - 1u) << ((int)(ku % upw) * ub));
   return __ldcg(bits + wd) & ~__ldg(heavy + wd) & sel;
+}
+
+// units per bitmap word for a pass over level L: fine units when the level
+// holds an eighth of the vertices or more (every thread decides alike)
+__device__ __forceinline__ int level_upw(const int32_t *lcount, int L, int64_t n) {
+  int64_t c = 0;
+#pragma unroll
+  for (int h = 0; h < WIDE_SHARDS; h++) c += __ldcg(lcount + ((size_t)L * WIDE_SHARDS + h) * 32);
+  return 8 * c >= n ? WIDE_UPW : 1;
 }
 
 template <int SPL>
@@ -249,6 +264,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       if (lane == 0) {
         S.flag[0] = 1;
         S.lkind[0] = 1;
+        S.lcount[0] = SB;
       }
     }
     if (!grid_wait(bar)) return;
@@ -292,6 +308,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
 #pragma unroll
       for (int q = 0; q < SPL; q++) wmax[q] = 0ull;
       bool found = false;
+      int nfirst = 0;  // first reaches this warp made (lane 0's count)
       // one vertex (its whole row, or one item of a long row)
       auto visit = [&](int32_t v, int64_t e0, int64_t e1) {
         bool on[SPL];
@@ -348,19 +365,22 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
           const unsigned frw = __reduce_or_sync(0xffffffffu, fr);
           if ((frw >> lane) & 1u) atomicOr(bits_next + (uj >> 5), 1u << (uj & 31));
           found |= frw != 0u;
+          nfirst += __popc(frw);
           __syncwarp();
         }
       };
       // work: the items of long rows (the longest work) first, then the
       // bitmap's words (light rows), handed out WIDE_GRAB at a time
       int shard = (int)((gtid >> 5) % WIDE_SHARDS);
+      const int upw = level_upw(S.lcount, L, S.n);
+      const int64_t total = S.nwords * upw + nh;
       for (;;) {
-        const int64_t w0 = wide_grab(S.wctr + (size_t)2 * L * WIDE_SHARDS * 32, S.nwords * WIDE_UPW + nh, shard, lane);
+        const int64_t w0 = wide_grab(S.wctr + (size_t)2 * L * WIDE_SHARDS * 32, total, shard, lane);
         if (w0 < 0) break;
-        for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords * WIDE_UPW + nh); wi++) {
+        for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, total); wi++) {
           if (wi >= nh) {
             int64_t wd;
-            uint32_t m = unit_bits(bits_cur, S.heavy, wi - nh, wd);
+            uint32_t m = unit_bits(bits_cur, S.heavy, wi - nh, upw, wd);
             while (m) {
               const int32_t v = (int32_t)(wd * 32 + __ffs(m) - 1);
               m &= m - 1u;
@@ -380,6 +400,8 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
       for (int q = 0; q < SPL; q++)
         if (wmax[q]) atomicMax(S.lmax + (size_t)L * SB + 32 * q + lane, wmax[q]);
       if (__any_sync(0xffffffffu, found) && lane == 0) S.flag[L + 1] = 1;
+      if (lane == 0 && nfirst)
+        atomicAdd(S.lcount + ((size_t)(L + 1) * WIDE_SHARDS + (gtid >> 5) % WIDE_SHARDS) * 32, nfirst);
       if (!grid_wait(bar)) return;
       mark(0x1000u | (unsigned)L);
 #pragma unroll
@@ -464,13 +486,15 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
         }
       };
       int shard = (int)((gtid >> 5) % WIDE_SHARDS);
+      const int upw = level_upw(S.lcount, l, S.n);
+      const int64_t total = S.nwords * upw + nh;
       for (;;) {
-        const int64_t w0 = wide_grab(S.wctr + (size_t)(2 * l + 1) * WIDE_SHARDS * 32, S.nwords * WIDE_UPW + nh, shard, lane);
+        const int64_t w0 = wide_grab(S.wctr + (size_t)(2 * l + 1) * WIDE_SHARDS * 32, total, shard, lane);
         if (w0 < 0) break;
-        for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, S.nwords * WIDE_UPW + nh); wi++) {
+        for (int64_t wi = w0; wi < min((int64_t)w0 + WIDE_GRAB, total); wi++) {
           if (wi >= nh) {
             int64_t wd;
-            uint32_t m = unit_bits(bits_l, S.heavy, wi - nh, wd);
+            uint32_t m = unit_bits(bits_l, S.heavy, wi - nh, upw, wd);
             while (m) {
               const int32_t v = (int32_t)(wd * 32 + __ffs(m) - 1);
               m &= m - 1u;
@@ -499,6 +523,7 @@ __global__ void __launch_bounds__(WIDE_THREADS, MINB) k_bcreach_wide(
         if (i < (int64_t)(Lmax + 2) * SB) S.lmax[i] = 0ull;
         if (i < Lmax + 3) S.flag[i] = 0;
         if (i < 2 * (Lmax + 2) * WIDE_SHARDS) S.wctr[i * 32] = 0;
+        if (i < (Lmax + 2) * WIDE_SHARDS) S.lcount[i * 32] = 0;
       }
       for (int64_t i = gtid; i < (int64_t)nhv * SB; i += nthreads) {  // long rows' slots (items shared them)
         const size_t x = (size_t)__ldg(S.hlist + (i / SB)) * SB + (i % SB);
@@ -578,7 +603,7 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
   DBuf<uint8_t> lvl;
   DBuf<double> sig, dsum;
   DBuf<uint32_t> bits, heavy;
-  DBuf<int32_t> flag, wctr, kshift, lkind, hlist, hv, hc, counts;
+  DBuf<int32_t> flag, wctr, lcount, kshift, lkind, hlist, hv, hc, counts;
   DBuf<unsigned long long> lmax, barw, trace;
   const bool tracing = std::getenv("BCS_TRACE") != nullptr;
   if (tracing) {
@@ -592,6 +617,7 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
   BCS_TRY(heavy.alloc(nwords, s));
   BCS_TRY(flag.alloc(lcap + 1, s));
   BCS_TRY(wctr.alloc((size_t)2 * lcap * WIDE_SHARDS * 32, s));
+  BCS_TRY(lcount.alloc((size_t)(lcap + 1) * WIDE_SHARDS * 32, s));
   BCS_TRY(kshift.alloc((size_t)lcap * SB, s));
   BCS_TRY(lkind.alloc(lcap + 1, s));
   BCS_TRY(lmax.alloc((size_t)lcap * SB, s));
@@ -607,6 +633,7 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
   BCS_CUDA(cudaMemsetAsync(heavy.p, 0, nwords * 4, s));
   BCS_CUDA(cudaMemsetAsync(flag.p, 0, (lcap + 1) * 4, s));
   BCS_CUDA(cudaMemsetAsync(wctr.p, 0, (size_t)2 * lcap * WIDE_SHARDS * 32 * 4, s));
+  BCS_CUDA(cudaMemsetAsync(lcount.p, 0, (size_t)(lcap + 1) * WIDE_SHARDS * 32 * 4, s));
   BCS_CUDA(cudaMemsetAsync(lmax.p, 0, (size_t)lcap * SB * 8, s));
   BCS_CUDA(cudaMemsetAsync(counts.p, 0, 8, s));
   BCS_CUDA(cudaMemsetAsync(barw.p, 0, 8, s));
@@ -615,7 +642,7 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
       n, row, heavy.p, hlist.p, hv.p, hc.p, counts.p);
   ctx.launches++;
   BCS_CUDA(cudaGetLastError());
-  WideScratch S{lvl.p,   sig.p,   dsum.p,   bits.p,  flag.p,  wctr.p,    lmax.p, kshift.p, lkind.p, heavy.p,
+  WideScratch S{lvl.p,   sig.p,   dsum.p,   bits.p,  flag.p,  wctr.p,    lcount.p, lmax.p, kshift.p, lkind.p, heavy.p,
                 hv.p,    hc.p,    hlist.p,  counts.p, tracing ? trace.p : nullptr, n, nwords, lcap};
   GridBarrier gb{(unsigned int *)barw.p, (unsigned int *)barw.p + 1, d_err, (long long)ctx.max_wait};
   const int32_t *colp = in.col;

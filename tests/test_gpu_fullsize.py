@@ -53,3 +53,17 @@ def test_twins_full_size_shattered_vs_plain(gpu):
     assert rel(b64, plain) <= TOL64
     b32 = gpu.bc_shattered(rp, col, delta_fp32=True).cpu().numpy()
     assert rel(b32, plain) <= TOL32
+
+
+def test_road_full_size_fp32_against_fp64_on_sampled_sources(gpu):
+    """The road-like workload (n = 2,258,525; BFS depth in the thousands,
+    where an FP32 dependency recurrence has the most levels to drift over):
+    plain Brandes partial sums over 512 seeded sources with FP32
+    dependencies against the same sums in FP64, within the 1e-5 bar."""
+    g = gg.config(4)
+    rp, col = on_device(g)
+    src = np.random.default_rng(44).choice(g.n, 512, replace=False)
+    b64 = gpu.bc_sources(rp, col, src).cpu().numpy()
+    b32 = gpu.bc_sources(rp, col, src, delta_fp32=True).cpu().numpy()
+    err = rel(b32, b64)
+    assert err <= TOL32, err

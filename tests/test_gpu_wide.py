@@ -83,9 +83,9 @@ def test_wide_shattered_reach_and_ident(gpu, wide_all, seed):
 
 
 def test_wide_split_rows(gpu, wide_all):
-    """Hubs of degree above the 256 row entries one warp takes: their rows
-    are cut into items spread over several warps (the five largest hubs
-    among the sources)."""
+    """Hubs of degree far above the long-row item (64 entries): their rows
+    are cut into items spread over many warps (the five largest hubs among
+    the sources)."""
     g = largest_component(gg.chung_lu(20000, 2.0, 12.0, 3))
     deg = np.diff(g.row_ptr)
     assert deg.max() > 512
@@ -97,7 +97,7 @@ def test_wide_split_rows(gpu, wide_all):
 
 
 def test_wide_path_counts_past_int64_and_double(gpu, wide_all):
-    """Layers of 400 vertices (rows of 800 entries, split over four warps):
+    """Layers of 400 vertices (rows of 800 entries, cut into 13 items):
     path counts grow by 400 per level, leave the 64-bit integers after 7
     levels and the double range (400^119 ~ 2^1029) before the last layer."""
     k, layers = 400, 120
