@@ -40,12 +40,14 @@
  * launch and a device-wide synchronisation).
  *
  * Environment: BCS_TRACE (any value) prints per-stage timings to stderr;
- * BCS_LARGE_PATH=wide|batched|per_source forces the kernel used for pieces
- * too large for shared memory (the whole GPU on one batch of 32 sources, 32
- * sources per CTA, or one), which is otherwise chosen from the piece's size,
- * its BFS depth, the number of sources and the memory each kernel needs;
- * BCS_LARGE_PATH=wide_all (for tests) sends every piece through the
- * whole-GPU kernel where its depth allows.
+ * BCS_LARGE_PATH=wide|batched|per_source|mid forces the kernel used for
+ * pieces too large for shared memory (the whole GPU on one batch of 64
+ * sources, 32 sources per CTA, one source per CTA, or one 64-source batch
+ * per CTA for pieces of at most 65,536 vertices), which is otherwise chosen
+ * from the pieces' sizes and count, their BFS depth, the number of sources
+ * and the memory each kernel needs (or by the autotuner);
+ * BCS_LARGE_PATH=wide_all|mid_all (for tests) sends every piece through the
+ * whole-GPU kernel, or the one-batch-per-CTA kernel, where its depth allows.
  */
 #ifndef BCSHATTER_H
 #define BCSHATTER_H

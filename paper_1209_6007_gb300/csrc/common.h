@@ -273,7 +273,7 @@ struct BcInput {
   double *bcp = nullptr;          // accumulation target, indexed by vertex
 };
 
-enum { LARGE_PATH_AUTO = 0, LARGE_PATH_WIDE = 1, LARGE_PATH_BATCHED = 2, LARGE_PATH_PER_SOURCE = 3 };
+enum { LARGE_PATH_AUTO = 0, LARGE_PATH_WIDE = 1, LARGE_PATH_BATCHED = 2, LARGE_PATH_PER_SOURCE = 3, LARGE_PATH_MID = 4 };
 
 struct BcPlanOpts {
   bool fp32_delta = false;
@@ -321,6 +321,13 @@ int run_wide(Ctx &ctx, const CompDesc &c, const BcInput &in, bool fp32, const in
              int depth_bound, int *d_err, unsigned long long *d_dag);
 // deepest BFS level run_wide can index
 int wide_depth_limit();
+// Bc-Reach over the listed mid-size pieces (every vertex a source, or with
+// d_order the one piece's sources), one 64-source batch per CTA at a time
+// (wide.cu).  d_comps: the device copy of comps.  Pieces found too deep for
+// its level cap, or not connected, are left undone and listed in too_deep.
+int run_mid(Ctx &ctx, const std::vector<CompDesc> &comps, const std::vector<int32_t> &pieces, const BcInput &in,
+            bool fp32, const int32_t *d_order, const CompDesc *d_comps, int *d_err, unsigned long long *d_dag,
+            std::vector<int32_t> *too_deep);
 // BFS of a connected graph from `root` (rows at rp[v]..rp[v+1] of col):
 // queue_out[0..*reached) the vertices in the order the search reaches them,
 // *depth the deepest level (order.cu)

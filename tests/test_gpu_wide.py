@@ -1,8 +1,9 @@
-"""The whole-GPU Bc-Reach kernel (large pieces of small BFS depth) against
-the oracle, through the C ABI (needs a CUDA device).
+"""The whole-GPU Bc-Reach kernel (large pieces of small BFS depth) and the
+one-batch-per-CTA kernel of mid-size pieces (the same batch, its waits
+CTA-wide) against the oracle, through the C ABI (needs a CUDA device).
 
-BCS_LARGE_PATH=wide_all sends every piece, however small, through that
-kernel, so graphs the oracle finishes in seconds cover it: source batches
+BCS_LARGE_PATH=wide_all|mid_all sends every piece, however small, through
+one of them, so graphs the oracle finishes in seconds cover them: source batches
 with a ragged end and repeated sources, reach and ident from shattering,
 rows long enough to be split over several warps, and path counts past the
 64-bit integers and past the double range.  Bars as in test_gpu_parity.py.
@@ -51,9 +52,12 @@ def layered(k, layers):
     return gg.from_edges(k * layers, np.concatenate(e))
 
 
-@pytest.fixture
-def wide_all(monkeypatch):
-    monkeypatch.setenv("BCS_LARGE_PATH", "wide_all")
+@pytest.fixture(params=["wide_all", "mid_all"])
+def wide_all(monkeypatch, request):
+    """Every piece on the whole-GPU kernel, or on the one-batch-per-CTA
+    kernel of mid-size pieces (the same batch, its waits CTA-wide)."""
+    monkeypatch.setenv("BCS_LARGE_PATH", request.param)
+    return request.param
 
 
 @pytest.mark.parametrize("per_batch", [32, 64])
@@ -66,7 +70,8 @@ def test_wide_plain_and_repeated_sources(gpu, wide_all, monkeypatch, per_batch):
     ref = oracle.bc(g)
     for fp32, tol in ((False, TOL64), (True, TOL32)):
         assert rel(gpu.bc_plain(g.row_ptr, g.col, delta_fp32=fp32), ref) <= tol
-        assert gpu.last_stats()["n_wide_batches"] == (g.n + per_batch - 1) // per_batch
+        per = per_batch if wide_all == "wide_all" else 64  # the mid-size kernel's batches are 64 sources
+        assert gpu.last_stats()["n_wide_batches"] == (g.n + per - 1) // per
     src = np.concatenate([np.random.default_rng(1).choice(g.n, 40, replace=False), [5, 5, 9, 9, 0]])
     assert rel(gpu.bc_sources(g.row_ptr, g.col, src), oracle.bc_sources(g, src)) <= TOL64
 
@@ -96,10 +101,31 @@ def test_wide_split_rows(gpu, wide_all):
     assert rel(gpu.bc_sources(g.row_ptr, g.col, src, delta_fp32=True), ref) <= TOL32
 
 
+def test_mid_path_counts_past_int64(gpu, monkeypatch):
+    """The one-batch-per-CTA kernel on layers of 400 vertices, 28 deep (path
+    counts leave the 64-bit integers after 7 levels), with a graph too deep
+    for its levels (a path of 100) in the same call: that piece falls back to
+    one source per CTA."""
+    monkeypatch.setenv("BCS_LARGE_PATH", "mid_all")
+    k, layers = 400, 28
+    g = layered(k, layers)
+    src = np.array([0, 1, 199, 10 * k + 3, k * layers - 1])
+    ref = oracle.bc_sources(g, src)
+    assert rel(gpu.bc_sources(g.row_ptr, g.col, src), ref) <= TOL64
+    assert rel(gpu.bc_sources(g.row_ptr, g.col, src, delta_fp32=True), ref) <= TOL32
+    assert gpu.last_stats()["n_wide_batches"] == 1
+    h = gg.disjoint_union(layered(30, 12), gg.path(100), gg.cycle(300))
+    assert rel(gpu.bc_shattered(h.row_ptr, h.col, steps=oracle.STEP_I), oracle.bc(h)) <= TOL64
+
+
 def test_wide_path_counts_past_int64_and_double(gpu, wide_all):
     """Layers of 400 vertices (rows of 800 entries, cut into 13 items):
     path counts grow by 400 per level, leave the 64-bit integers after 7
-    levels and the double range (400^119 ~ 2^1029) before the last layer."""
+    levels and the double range (400^119 ~ 2^1029) before the last layer.
+    (Whole-GPU kernel only: 120 layers are deeper than the mid-size kernel's
+    levels; test_mid_path_counts_past_int64 covers that kernel.)"""
+    if wide_all == "mid_all":
+        pytest.skip("deeper than the mid-size kernel's level cap")
     k, layers = 400, 120
     g = layered(k, layers)
     src = np.array([0, 1, 199, 70 * k + 3, k * layers - 1])
@@ -119,6 +145,9 @@ def test_wide_device_input_and_several_components(gpu, wide_all):
     assert rel(gpu.bc_plain(rp, col).cpu().numpy(), ref) <= TOL64
     h = gg.disjoint_union(gg.cycle(40), g, gg.path(7), gg.star(5), gg.gnp(1, 0.5, 0))
     assert rel(gpu.bc_plain(h.row_ptr, h.col), oracle.bc(h)) <= TOL64
-    assert gpu.last_stats()["n_wide_batches"] > 0
+    if wide_all == "wide_all":
+        assert gpu.last_stats()["n_wide_batches"] > 0
+    else:  # one piece that is not connected: left to one source per CTA
+        assert gpu.last_stats()["n_wide_batches"] == 0
     src = np.array([0, 39, 40, 41, h.n - 1, h.n - 2, 45])
     assert rel(gpu.bc_sources(h.row_ptr, h.col, src, delta_fp32=True), oracle.bc_sources(h, src)) <= TOL32
