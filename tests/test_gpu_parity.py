@@ -574,8 +574,8 @@ def test_fixpoint_loop_on_blown_up_graphs(gpu, unequal):
 
 def test_fixpoint_loop_on_a_nested_four_cycle(gpu):
     """C4 blown up: the first merge takes each pair of opposite corner groups
-    into one vertex, leaving one edge; round 1 splits it off and merges its
-    closed pair, round 2 finds nothing left to merge."""
+    into one vertex, leaving one edge; the first split-and-merge round splits
+    it off and merges its closed pair, the second finds nothing to merge."""
     g = gg.blow_up(gg.cycle(4), 3, max_k=3, p_closed=0.0)
     assert rel(gpu.bc_shattered(g.row_ptr, g.col, resplit=True), oracle.bc(g)) <= TOL64
     assert gpu.last_stats()["n_rounds"] == 2
