@@ -272,7 +272,8 @@ def roofline(st: dict, clk: dict, peaks: dict, n_sm: int) -> dict:
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (of measured)" if "hbm_gbs" in peaks else "fallback",
                 "work": {"bytes": by, "f_dag": f_dag, "sources_x_entries": wse, "sources_x_vertices": wsv,
                          "batches": int(st["n_wide_batches"]), "ms": ms,
-                         "traffic_scaled_from": "ncu DRAM bytes of one 32-source batch x batches" if traffic else None}}
+                         "traffic_scaled_from": "ncu DRAM bytes of a full launch per batch (profiles/bcreach_wide_twins.json) "
+                                                "x this call's batches" if traffic else None}}
     flop = 2.0 * dag + 9.0 * wsv
     ms = st["ms_bcreach_small"]
     fp64_peak = n_sm * 4.0 * sm_mhz * 1e6 / 1e12
