@@ -1,6 +1,8 @@
 // wide.cu - Bc-Reach (Algorithm 2 with the identical-vertex terms of
 // Section 3.3.3) on one large piece of small BFS depth, with every SM of the
-// GPU working on one batch of 64 (or 32) sources at a time.
+// GPU working on one batch of 64 (or 32) sources at a time; and the same
+// batch on one CTA at a time for many mid-size pieces (k_bcreach_mid, at the
+// end of the file).
 //
 // Why the whole GPU on one batch: on a small-world piece (hundreds of
 // thousands of vertices, a handful of BFS levels) the per-vertex records of a
