@@ -154,7 +154,8 @@ typedef struct bcs_stats {
   int64_t small_smem_budget; /* shared-memory budget per small-path CTA (bytes) */
   int64_t n_side;          /* side vertices taken out of the pieces (BCS_STEP_S) */
   int64_t n_wide_batches;  /* source batches (64, or 32) run with the whole GPU on
-                              one batch (large pieces of small BFS depth) */
+                              one batch (large pieces of small BFS depth), or one
+                              per CTA on mid-size pieces (BCS_LARGE_PATH=mid) */
   int64_t n_rounds;        /* split-and-merge rounds of the preprocessing loop
                               (BCS_STEP_L) */
   int64_t small_limit;     /* shared memory (bytes) a piece may need for one source
